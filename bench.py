@@ -1,0 +1,513 @@
+#!/usr/bin/env python
+"""Benchmark of the batched finite-volume patch update on GB300.
+
+Workload (default): 16,384 two-dimensional patches of 16 x 16 volumes with a
+one-volume fixed halo, compressible Euler (4 unknowns, gamma 1.4), Rusanov
+flux, explicit Euler step with per-patch CFL 0.4 time steps, dx = 0.01,
+seeded uniform primitives (rho, p in [0.5, 1.5], u, v in [-0.5, 0.5]).
+
+One benchmark "step" is one time step of the whole batch: one call of
+``fv_patch_batch_update`` (stage, directional fluxes and eigenvalues, Rusanov
+face fluxes, update, per-patch eigenvalue maximum and next CFL time step).
+The headline value is the fused FP32 form; the FP64 fused and the plain FP64
+loop-cascade forms are timed beside it.  L2 is flushed (256 MiB write)
+before every timed step and each step is timed alone with CUDA events on the
+launching stream.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (the reference arm of this project).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "volume updates/s per GB300 (2D Euler Rusanov FV step, fused FP32 vs plain FP64 cascade)"
+UNIT = "volume updates/s"
+WORKLOAD = "2D Euler, 16384 patches of 16x16 + 1-cell fixed halo, dx=0.01, CFL 0.4, seeded uniform primitives"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--profile", choices=["fused_f32", "fused_f64", "cascade_f64", "tile_f32"],
+                    default=None, help="no timing: run a few launches of one form for ncu")
+    ap.add_argument("--patches", type=int, default=None,
+                    help="with --profile: batch size (default 65536, state larger than L2)")
+    return ap.parse_args()
+
+
+def algorithmic_bytes_per_volume(dim, p, N, s, periodic=False):
+    """Read every needed volume once (interior plus the 2d face-halo layers;
+    periodic halos are rebuilt from the interior), write the interior once."""
+    reads = p ** dim + (0 if periodic else 2 * dim * p ** (dim - 1))
+    return N * s * (reads + p ** dim) / p ** dim
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        busy = [c for c, p in zip(sm, power) if p > 200.0] or sm
+        return {"sm_mhz": float(np.median(busy)) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def _oracle_sample(w, idx):
+    off = w.offsets()
+    return np.concatenate([np.asarray(w.Q0[off[i]:off[i + 1]], dtype=np.float64) for i in idx])
+
+
+def cpu_baseline(w, seconds, sample_patches=1024, steps=1):
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(12345)
+    idx = np.sort(rng.choice(w.num_patches, min(sample_patches, w.num_patches), replace=False))
+    Q = _oracle_sample(w, idx)
+    psz, dx = w.patch_size[idx], w.dx[idx]
+    vols = int(np.sum(psz.astype(np.int64) ** w.dim))
+    lam = oracle.batch_max_eigenvalue(w.dim, psz, Q)
+    dt = oracle.cfl_time_step(w.dim, lam, dx, w.cfl)
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        for _ in range(steps):
+            oracle.batch_step(w.dim, psz, dx, dt, Q, w.gamma, w.halo_mode)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    value = vols * steps * runs / el
+    desc = ("%d seeded patches of the workload x %d step(s), repeated %d times (%.1f s)"
+            % (len(idx), steps, runs, el))
+    return value, oracle.num_threads(), desc
+
+
+def oracle_error(w, Q0_f32, gpu_final, steps, idx):
+    """rel L-inf of the GPU result on patches idx vs the FP64 oracle run from
+    the same (FP32-rounded) start, with its own CFL chain."""
+    import oracle
+    start = _oracle_sample(w, idx).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    ref, _, _ = oracle.batch_run(w.dim, w.patch_size[idx], w.dx[idx], start, steps,
+                                 w.gamma, w.halo_mode, w.cfl)
+    el = time.perf_counter() - t0
+    off = w.offsets()
+    got = np.concatenate([gpu_final[off[i]:off[i + 1]] for i in idx])
+    N = w.dim + 2
+    errs = []
+    o2 = np.concatenate([[0], np.cumsum((N) * (w.patch_size[idx].astype(np.int64) + 2) ** w.dim)])
+    A, B = [], []
+    for j, i in enumerate(idx):
+        p = int(w.patch_size[i])
+        sh = (p + 2,) * w.dim + (N,)
+        A.append(got[o2[j]:o2[j + 1]].reshape(sh)[(slice(1, -1),) * w.dim].reshape(-1, N))
+        B.append(ref[o2[j]:o2[j + 1]].reshape(sh)[(slice(1, -1),) * w.dim].reshape(-1, N))
+    A, B = np.concatenate(A), np.concatenate(B)
+    for k in range(N):
+        errs.append(np.max(np.abs(A[:, k] - B[:, k])) / np.max(np.abs(B[:, k])))
+    return float(max(errs)), el
+
+
+# ------------------------------------------------------------ traffic note
+
+def committed_traffic(kernel_tag, source_files):
+    """DRAM bytes per launch from a committed ncu summary, valid only while
+    the kernel sources still hash to the value recorded beside it."""
+    path = os.path.join(ROOT, "profiles", kernel_tag + ".md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h:
+        return None
+    sha = hashlib.sha256()
+    for f in source_files:
+        sha.update(open(os.path.join(ROOT, f), "rb").read())
+    if sha.hexdigest()[:16] != h.group(1)[:16]:
+        return None
+    return float(m.group(1))
+
+
+def kernel_source_files():
+    c = "paper_2306_16731_gb300/csrc/"
+    return [c + "fv_sweep.cu", c + "fv_physics.cuh", c + "fv_common.cuh"]
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(args):
+    import torch
+    from paper_2306_16731_gb300 import build, fvbatch as fb, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    build.build()
+
+    w = inputs.config(2, dtype=np.float32)
+    N, T, p = w.dim + 2, w.num_patches, int(w.patch_size[0])
+    vols = w.interior_volumes
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def make(precision, form):
+        b = fb.FVBatch(w.dim, w.patch_size, precision=precision, halo_mode=w.halo_mode,
+                       form=form, stream=stream.cuda_stream)
+        dtype = {0: torch.float64, 1: torch.float32}[precision]
+        qa = torch.from_numpy(w.Q0).to(device=dev, dtype=dtype)
+        qb = qa.clone()
+        dx = torch.tensor(w.dx, device=dev)
+        lam = torch.zeros(T, dtype=torch.float64, device=dev)
+        dta, dtb = torch.zeros_like(lam), torch.zeros_like(lam)
+        b.max_eigenvalue(qa, lam)
+        b.cfl_time_step(lam, dx, w.cfl, dta)
+        return b, [qa, qb], dx, lam, [dta, dtb]
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed_steps(b, qs, dx, lam, dts, steps, warmup):
+        for s in range(warmup):
+            i = s & 1
+            b.update(qs[i], qs[1 - i], dx, dts[i], lam, dts[1 - i], w.cfl)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        for s in range(steps):
+            i = (warmup + s) & 1
+            flush.zero_()
+            ev[s][0].record(stream)
+            b.update(qs[i], qs[1 - i], dx, dts[i], lam, dts[1 - i], w.cfl)
+            ev[s][1].record(stream)
+        barrier()
+        return sum(a.elapsed_time(c) for a, c in ev)     # ms
+
+    clocks = ClockSampler(_smi_id(torch, dev))
+    clocks.start()
+
+    # headline: fused FP32
+    b32, qs32, dx, lam32, dts32 = make(fb.FV_F32, fb.FV_FORM_FUSED if _fused_ok(fb, w, fb.FV_F32) else fb.FV_FORM_TILE)
+    scratch = qs32[0].clone()
+    b32.tune(qs32[0], scratch, dx, dts32[0])
+    del scratch
+    ms = timed_steps(b32, qs32, dx, lam32, dts32, args.steps, args.warmup)
+    desc32 = b32.describe()
+    launches = b32.launches_per_update() * args.steps
+
+    # max over ranks
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * vols * args.steps / (ms_max / 1e3)
+
+    # the FP64 forms beside it (fewer steps: FP64 is slow on this part)
+    forms = {}
+    k64 = max(5, min(20, args.steps // 10))
+    for name, prec, form in (("fused_f64", fb.FV_F64, fb.FV_FORM_FUSED),
+                             ("tile_f64", fb.FV_F64, fb.FV_FORM_TILE),
+                             ("cascade_f64", fb.FV_F64, fb.FV_FORM_CASCADE),
+                             ("tile_f32", fb.FV_F32, fb.FV_FORM_TILE),
+                             ("cascade_f32", fb.FV_F32, fb.FV_FORM_CASCADE)):
+        try:
+            bb, qq, dxx, ll, dd = make(prec, form)
+        except fb.FVError:
+            continue
+        m = timed_steps(bb, qq, dxx, ll, dd, k64, 3)
+        forms[name] = {"value": vols * k64 / (m / 1e3), "ms_per_step": m / k64,
+                       "launches_per_step": bb.launches_per_update(), "kernel": bb.describe()}
+        bb.close()
+        del qq
+    forms["fused_f32"] = {"value": vols * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                          "launches_per_step": b32.launches_per_update(), "kernel": desc32}
+
+    # 100-step graph-captured run from the initial state, L2-warm (for the
+    # error statement and the multi-step throughput)
+    qa = torch.from_numpy(w.Q0).to(device=dev, dtype=torch.float32)
+    qb = qa.clone()
+    b32.max_eigenvalue(qa, lam32)
+    b32.cfl_time_step(lam32, dx, w.cfl, dts32[0])
+    b32.run(qa, qb, dx, dts32[0], dts32[1], lam32, w.steps, w.cfl, True)   # capture + run
+    qa2 = torch.from_numpy(w.Q0).to(device=dev, dtype=torch.float32)
+    qa.copy_(qa2)
+    qb.copy_(qa2)
+    del qa2
+    b32.max_eigenvalue(qa, lam32)
+    b32.cfl_time_step(lam32, dx, w.cfl, dts32[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b32.run(qa, qb, dx, dts32[0], dts32[1], lam32, w.steps, w.cfl, True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b32.status()
+    graph_ms = e0.elapsed_time(e1)
+    final = (qb if w.steps % 2 else qa).to(torch.float64).cpu().numpy()
+    forms["fused_f32_graph_%dsteps_l2warm" % w.steps] = {
+        "value": vols * w.steps / (graph_ms / 1e3), "ms_per_step": graph_ms / w.steps}
+
+    # end to end through the public API with host buffers
+    host_in = torch.from_numpy(w.Q0.astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    host_dt = torch.full((T,), 1e-3, dtype=torch.float64).pin_memory()
+    host_dx = torch.from_numpy(w.dx.copy()).pin_memory()
+    host_lam = torch.empty(T, dtype=torch.float64).pin_memory()
+    qd_in, qd_out = qs32[0], qs32[1]
+    qd_out.copy_(qd_in)
+    dtd = torch.empty(T, dtype=torch.float64, device=dev)
+    ke = max(5, min(50, args.steps // 4))
+    for s in range(3 + ke):
+        if s == 3:
+            barrier()
+            t_e2e = time.perf_counter()
+            ee0 = torch.cuda.Event(enable_timing=True)
+            ee0.record(stream)
+        qd_in.copy_(host_in, non_blocking=True)
+        dx.copy_(host_dx, non_blocking=True)
+        dtd.copy_(host_dt, non_blocking=True)
+        b32.update(qd_in, qd_out, dx, dtd, lam32, None, w.cfl)
+        host_out.copy_(qd_out, non_blocking=True)
+        host_lam.copy_(lam32, non_blocking=True)
+        stream.synchronize()
+    ee1 = torch.cuda.Event(enable_timing=True)
+    ee1.record(stream)
+    barrier()
+    e2e_ms = ee0.elapsed_time(ee1)
+    state_bytes = host_in.numel() * 4
+    e2e = {"value": world * vols * ke / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(state_bytes + 2 * T * 8),
+           "d2h_bytes_per_step": int(state_bytes + T * 8),
+           "wall_s": time.perf_counter() - t_e2e}
+
+    clk = clocks.stop()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    bpv = algorithmic_bytes_per_volume(w.dim, p, N, 4)
+    avg_launch_s = (ms / args.steps) / 1e3
+    achieved = vols * bpv / avg_launch_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = committed_traffic("fused_f32_2d_p16_T16384", kernel_source_files())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes_per_volume": bpv,
+                "algorithmic_bytes_per_launch": vols * bpv,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks
+                else "fallback 6800 GB/s"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded PCG64 uniform primitives; no dataset)",
+           "config": {"workload": WORKLOAD, "dim": 2, "patches_per_gpu": T, "p": p,
+                      "unknowns": N, "precision": "f32 state and arithmetic, f64 eigenvalue "
+                      "maximum and CFL time step", "form": "fused", "kernel": desc32,
+                      "l2": "flushed before every timed step (256 MiB write); steps timed "
+                            "one by one with CUDA events",
+                      "parallelism": "replicas (patches independent; no collective)"},
+           "roofline": roofline, "gpu_launches": launches, "e2e": e2e, "clocks": clk,
+           "forms": forms}
+    if "cascade_f64" in forms:
+        out["speedup_fused_f32_vs_cascade_f64"] = forms["fused_f32"]["value"] / forms["cascade_f64"]["value"]
+
+    if not args.no_cpu_baseline and world == 1:
+        wd = inputs.config(2, dtype=np.float64)
+        v, cores, desc = cpu_baseline(wd, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": desc}
+        idx = np.sort(np.random.default_rng(7).choice(T, 16, replace=False))
+        err, _ = oracle_error(wd, None, final, w.steps, idx)
+        out["error_vs_oracle"] = {"rel_linf": err, "steps": w.steps, "precision": "f32",
+                                  "patches_sampled": len(idx),
+                                  "bound": 1e-5}
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def _smi_id(torch, dev):
+    """nvidia-smi selector of the torch device (its UUID when available)."""
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index or 0)
+
+
+def _fused_ok(fb, w, precision):
+    try:
+        b = fb.FVBatch(w.dim, w.patch_size, precision=precision, halo_mode=w.halo_mode,
+                       form=fb.FV_FORM_FUSED)
+        b.close()
+        return True
+    except fb.FVError:
+        return False
+
+
+# ------------------------------------------------------------- reference
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    from paper_2306_16731_gb300 import inputs
+    import oracle
+    oracle.build()
+    w = inputs.config(2, dtype=np.float64)
+    rng = np.random.default_rng(12345)
+    idx = np.sort(rng.choice(w.num_patches, 512, replace=False))
+    Q = _oracle_sample(w, idx)
+    psz, dx = w.patch_size[idx], w.dx[idx]
+    vols = int(np.sum(psz.astype(np.int64) ** w.dim))
+    lam = oracle.batch_max_eigenvalue(w.dim, psz, Q)
+    dt = oracle.cfl_time_step(w.dim, lam, dx, w.cfl)
+    cur = Q
+    for _ in range(args.warmup):
+        cur, lam = oracle.batch_step(w.dim, psz, dx, dt, cur, w.gamma, w.halo_mode)
+        dt = oracle.cfl_time_step(w.dim, lam, dx, w.cfl)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cur, lam = oracle.batch_step(w.dim, psz, dx, dt, cur, w.gamma, w.halo_mode)
+        dt = oracle.cfl_time_step(w.dim, lam, dx, w.cfl)
+    el = time.perf_counter() - t0
+    value = vols * args.steps / el
+    cores = oracle.num_threads()
+    sample = "512 seeded patches of the workload per step, FP64 oracle on %d host threads" % cores
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": 2, "patches_per_step": len(idx), "p": 16,
+                       "form": "FP64 CPU oracle (plain C, OpenMP over patches)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def run_profile(args):
+    """A few launches of one form on a batch larger than L2, for ncu."""
+    import torch
+    from paper_2306_16731_gb300 import build, fvbatch as fb, inputs
+    build.build()
+    T = args.patches or 65536
+    w = inputs.uniform_batch(2, [16] * T, seed=2, dx=0.01, dtype=np.float32)
+    form_name, prec_name = args.profile.split("_")
+    prec = {"f32": fb.FV_F32, "f64": fb.FV_F64}[prec_name]
+    form = {"fused": fb.FV_FORM_FUSED, "cascade": fb.FV_FORM_CASCADE, "tile": fb.FV_FORM_TILE}[form_name]
+    b = fb.FVBatch(2, w.patch_size, precision=prec, form=form)
+    dtype = torch.float32 if prec == fb.FV_F32 else torch.float64
+    qa = torch.from_numpy(w.Q0).to("cuda", dtype)
+    qb = qa.clone()
+    dx = torch.tensor(w.dx, device="cuda")
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dta, dtb = torch.zeros_like(lam), torch.zeros_like(lam)
+    b.max_eigenvalue(qa, lam)
+    b.cfl_time_step(lam, dx, 0.4, dta)
+    for s in range(args.warmup + args.steps):
+        i = s & 1
+        b.update([qa, qb][i], [qb, qa][i], dx, [dta, dtb][i], lam, [dtb, dta][i], 0.4)
+    torch.cuda.synchronize()
+    b.status()
+    print(json.dumps({"profile": args.profile, "patches": T, "launches": args.warmup + args.steps,
+                      "kernel": b.describe()}))
+
+
+def main():
+    args = parse_args()
+    if args.profile:
+        run_profile(args)
+        return
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * fv_batch.h -- C ABI of the GB300 (sm_103a) batched finite-volume patch
+ * update: one explicit Euler time step of T Cartesian patches with a
+ * one-volume halo, Rusanov face fluxes on the compressible Euler equations,
+ * and the per-patch maximum eigenvalue that feeds the CFL condition.
+ *
+ * Method: arXiv:2306.16731, "SYCL compute kernels for ExaHyPE".
+ *   - Sec. 2.2: volume update from face fluxes, Rusanov flux (Eq. 2), halo
+ *     layer of width one, per-patch maximum eigenvalue of the new solution
+ *     for the CFL condition (local time stepping).
+ *   - Sec. 2.3: the kernel takes N (p+2)^d T values (with halo) and yields
+ *     the N p^d T interior values of the next time step; Algorithm 1 lists
+ *     its steps.
+ *   - Sec. 3: patch-wise, batched and task-graph realisations (the
+ *     "cascade" form below is the batched one, the "tile" form the
+ *     patch-wise one).
+ *   - Sec. 4: array-of-structures data layout, per-patch reductions.
+ *   - Sec. 5: Euler equations, N = d + 2 unknowns.
+ * Readings of passages the paper leaves garbled: the update is
+ * Q_new = Q - dt/h * sum_n (Fhat_n(c+1/2) - Fhat_n(c-1/2)); the Rusanov
+ * dissipation is 1/2 max(lambda_L, lambda_R) (Q_R - Q_L); the CFL time step
+ * is dt = cfl * h / (d * lambda_max).
+ *
+ * Data layout (all state buffers): array of structures with halo,
+ *   Q[patch][z][y][x][k],  x fastest, the N = d+2 unknowns of a volume
+ *   contiguous (rho, rho u_1 .. rho u_d, E); patch i starts at element
+ *   sum_{j<i} N (p_j + 2)^d.  Element type: double (FV_F64), float
+ *   (FV_F32) or bfloat16 (FV_BF16_F32).  fv_batch_state_elems() gives the
+ *   element count.  Buffers must be 16-byte aligned.
+ *
+ * Ownership: the caller owns every state, dx, dt, lambda and dt buffer and
+ * the CUDA stream; they are DEVICE pointers unless stated otherwise.  A
+ * batch owns only its metadata (patch offsets and sizes on the device, the
+ * kernel choice) and the scratch of the loop-cascade form.  Batches are not
+ * thread-safe: use one batch per host thread.
+ *
+ * Errors: every entry point returns FV_OK (0) or a negative FV_E* code and
+ * never aborts; fv_last_error() returns a thread-local message for the last
+ * failure.  Argument errors are reported synchronously.  Non-physical
+ * states met on the device (density or pressure not positive, eigenvalue
+ * not finite) set a device flag; fv_batch_status() synchronises the stream,
+ * reports FV_ENONPHYSICAL and clears the flag.  Update, eigenvalue, time
+ * step and totals calls are asynchronous on the batch's stream, allocate
+ * nothing and may be captured in a CUDA graph.
+ */
+#ifndef FV_BATCH_H
+#define FV_BATCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fv_batch fv_batch_t;
+
+/* Status codes. */
+enum {
+    FV_OK = 0,
+    FV_EINVAL = -1,         /* bad argument (size, pointer, alias, mode) */
+    FV_ENOMEM = -2,         /* host or device allocation failed */
+    FV_ECUDA = -3,          /* a CUDA runtime call failed */
+    FV_EUNSUPPORTED = -4,   /* valid request no kernel of this build covers */
+    FV_ENONPHYSICAL = -5    /* device met rho <= 0, p <= 0 or a non-finite eigenvalue */
+};
+
+/* Storage / compute precision of the state. */
+enum {
+    FV_F64 = 0,             /* double storage, double arithmetic */
+    FV_F32 = 1,             /* float storage, float arithmetic */
+    FV_BF16_F32 = 2         /* bfloat16 storage, float arithmetic */
+};
+/* In every precision the per-patch eigenvalue maximum, the CFL time step
+ * and the conservation totals are double. */
+
+/* Halo treatment (the halo layer of width one, Sec. 2.2). */
+enum {
+    FV_HALO_FIXED = 0,      /* halo volumes are read from Q_in as given; Q_out's halo is not written */
+    FV_HALO_PERIODIC = 1    /* halo volumes are the wrapped interior of the same patch; halo memory is never read or written */
+};
+
+/* Kernel realisation (Sec. 3). */
+enum {
+    FV_FORM_FUSED = 0,      /* default: one fused launch per step (warp-level sweep kernels) */
+    FV_FORM_CASCADE = 1,    /* one launch per algorithmic step over all volumes, intermediates in device memory (batched realisation) */
+    FV_FORM_TILE = 2        /* one thread block per patch staged in shared memory (patch-wise realisation) */
+};
+
+/*
+ * Create a batch of num_patches patches of dimension dim (2 or 3) with
+ * edge lengths patch_size[i] >= 1 (HOST array of num_patches entries; copied).
+ * halo must be 1 and unknowns must be dim + 2 (Euler).  precision is an
+ * FV_F64/FV_F32/FV_BF16_F32 value, halo_mode an FV_HALO_* value, gamma > 1
+ * the adiabatic index.  cuda_stream is a cudaStream_t (0 = legacy default
+ * stream) on which every later call of this batch runs.  The device current
+ * at creation is the batch's device.  On success *out receives the batch;
+ * on failure *out is NULL.
+ */
+int fv_batch_create(fv_batch_t **out, int dim, int num_patches,
+                    const int32_t *patch_size, int halo, int unknowns,
+                    int precision, int halo_mode, double gamma,
+                    void *cuda_stream);
+
+/* Select the kernel realisation (FV_FORM_*).  FV_EUNSUPPORTED if this
+ * build has no kernel of that form for the batch's shapes; the previous
+ * form stays selected.  May allocate the cascade's scratch (FV_ENOMEM). */
+int fv_batch_set_form(fv_batch_t *b, int form);
+
+/* Rebind the batch to another stream (e.g. a capture stream). */
+int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream);
+
+/*
+ * One explicit time step (Sec. 2.2, Eq. 2, Algorithm 1):
+ *   Q_out = Q_in - dt_i/dx_i * sum_n (Fhat_n(c+1/2) - Fhat_n(c-1/2))
+ * on the interior of every patch i.  Q_in and Q_out are device state
+ * buffers of the batch's layout and precision; Q_out != Q_in and they must
+ * not overlap (the update reads old neighbour values).  Only Q_out's
+ * interior is written.  dx and dt are device arrays of num_patches doubles
+ * (mesh width and time step per patch, > 0).  If lambda_out (device,
+ * num_patches doubles) is not NULL it receives the maximum over interior
+ * volumes and directions of |u_n| + c of Q_out; if dt_next_out is not NULL
+ * it receives cfl * dx_i / (dim * lambda_i) (requires cfl > 0).
+ */
+int fv_patch_batch_update(fv_batch_t *b, const void *Q_in, void *Q_out,
+                          const double *dx, const double *dt,
+                          double *lambda_out, double *dt_next_out, double cfl);
+
+/* Per-patch maximum eigenvalue of Q (Sec. 2.2, Sec. 4 "Reduction"):
+ * lambda_out[i] = max over interior volumes and directions n of |u_n| + c
+ * (device arrays). */
+int fv_max_eigenvalue(fv_batch_t *b, const void *Q, double *lambda_out);
+
+/* CFL time step per patch: dt_out[i] = cfl * dx[i] / (dim * lambda[i])
+ * (device arrays of num_patches doubles; cfl > 0). */
+int fv_cfl_time_step(fv_batch_t *b, const double *lambda, const double *dx,
+                     double cfl, double *dt_out);
+
+/* Conservation diagnostics: totals_out[i*N + k] = sum over the interior
+ * volumes of patch i of unknown k, accumulated in double (device array of
+ * num_patches * N doubles). */
+int fv_conserved_totals(fv_batch_t *b, const void *Q, double *totals_out);
+
+/*
+ * steps explicit steps with device-side CFL chaining, ping-ponging between
+ * two state buffers: step s reads Q_a (s even) or Q_b (s odd) and writes
+ * the other; dt_a holds the first step's time steps and dt_a/dt_b
+ * alternate as time-step buffers likewise.  lambda_out (may be NULL)
+ * receives the eigenvalues of the final state.  With use_graph != 0 the
+ * steps are captured once into a CUDA graph (cached per buffer set and
+ * step count) and replayed; the result is identical to eager launches.
+ * The final state is in Q_b if steps is odd, else in Q_a.
+ */
+int fv_batch_run(fv_batch_t *b, void *Q_a, void *Q_b, const double *dx,
+                 double *dt_a, double *dt_b, double *lambda_out, int steps,
+                 double cfl, int use_graph);
+
+/*
+ * Autotune the fused form: time every candidate launch shape of this
+ * batch's kernel on the given buffers (contents of Q_out are overwritten),
+ * check that every candidate's output is bitwise identical to the first
+ * one's, and keep the fastest.  Results are cached per device and batch
+ * shape in memory and, if the environment variable FVBATCH_TUNE_CACHE names
+ * a file, in that file.  Synchronises the stream.
+ */
+int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out,
+                  const double *dx, const double *dt);
+
+/* Synchronise the batch's stream and report FV_ENONPHYSICAL if any call
+ * since the last status check met a non-physical state (and clear it). */
+int fv_batch_status(fv_batch_t *b);
+
+/* Free the batch (NULL-safe).  Synchronises its stream first. */
+int fv_batch_destroy(fv_batch_t *b);
+
+/* Thread-local description of the last failure ("" if none). */
+const char *fv_last_error(void);
+
+/* Elements (not bytes) of one halo-inclusive state buffer of the batch. */
+size_t fv_batch_state_elems(const fv_batch_t *b);
+
+/* Device scratch bytes the batch holds (loop-cascade intermediates). */
+size_t fv_batch_scratch_bytes(const fv_batch_t *b);
+
+/* Write a one-line description of the selected kernels and launch shapes
+ * into buf (NUL-terminated, truncated to len). */
+int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len);
+
+/* Number of kernel launches one fv_patch_batch_update call makes with the
+ * current form and arguments (lambda/dt outputs present). */
+int fv_batch_launches_per_update(const fv_batch_t *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FV_BATCH_H */

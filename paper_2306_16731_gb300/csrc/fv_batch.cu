@@ -1,0 +1,665 @@
+// fv_batch.cu -- the C ABI declared in include/fv_batch.h: batch object,
+// argument validation, metadata upload, form selection, dispatch to the
+// kernel launchers, device-side CFL chaining over many steps with CUDA-graph
+// capture, the launch-shape autotuner and error reporting.
+//
+// The batch follows the paper's "managed memory" idiom (arXiv:2306.16731,
+// Sec. 4 "Data transfer"): device memory is reserved once at creation and
+// recycled by every later call; no call after creation allocates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/fv_batch.h"
+#include "fv_internal.h"
+#include "fv_physics.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(FV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int kMaxEdge2D = 1024;
+constexpr int kMaxEdge3D = 128;
+
+struct GraphKey {
+    const void *qa, *qb, *dx;
+    const double *dta, *dtb, *lam;
+    int steps;
+    double cfl;
+    int form;
+    bool operator<(const GraphKey &o) const
+    {
+        return std::tie(qa, qb, dx, dta, dtb, lam, steps, cfl, form) <
+               std::tie(o.qa, o.qb, o.dx, o.dta, o.dtb, o.lam, o.steps, o.cfl, o.form);
+    }
+};
+
+}  // namespace
+
+struct fv_batch {
+    int device = 0;
+    int dim = 2, T = 0, precision = 0, halo_mode = 0;
+    double gamma = 1.4;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    int form = FV_FORM_FUSED;
+
+    std::vector<int32_t> psize;
+    std::vector<int64_t> elem_off, cell_off, int_off;
+    int64_t state_elems = 0;
+
+    void *meta = nullptr;              // device metadata block
+    fv::BatchView view{};
+
+    void *scratch = nullptr;           // cascade intermediates
+    size_t scratch_bytes = 0;
+    fv::CascadeScratch cs{};
+
+    int fused_kernel = fv::FUSED_NONE;
+    fv::FusedPlan plan{};
+    std::vector<fv::WorkItem> items_h;
+
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+};
+
+namespace fv {
+
+int num_sms()
+{
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev] = n;
+    return n;
+}
+
+}  // namespace fv
+
+namespace {
+
+size_t elem_bytes(int precision) { return precision == FV_F64 ? 8 : (precision == FV_F32 ? 4 : 2); }
+
+// RAII: make the batch's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool overlaps(const void *a, const void *b, size_t bytes)
+{
+    uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bytes && y < x + bytes;
+}
+
+int ensure_scratch(fv_batch *b)
+{
+    if (b->scratch || b->T == 0) return FV_OK;
+    size_t bytes = fv::cascade_scratch_bytes(b->view, b->precision);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FV_ENOMEM, "cascade scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    b->scratch = p;
+    b->scratch_bytes = bytes;
+    fv::cascade_scratch_carve(p, b->view, b->precision, &b->cs);
+    return FV_OK;
+}
+
+void drop_graphs(fv_batch *b)
+{
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// Build the fused sweep work list: patches grouped by edge length (largest
+// first), groups cut into items of fv::fused_items_for() patches.
+void build_work_list(fv_batch *b, std::vector<int32_t> &order, std::vector<fv::WorkItem> &items)
+{
+    order.resize(b->T);
+    for (int i = 0; i < b->T; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return b->psize[a] > b->psize[c]; });
+    items.clear();
+    int i = 0;
+    while (i < b->T) {
+        int p = b->psize[order[i]];
+        int per = 1;
+        fv::fused_items_for(b->dim, p, &per);
+        int j = i;
+        while (j < b->T && b->psize[order[j]] == p) ++j;
+        for (int s = i; s < j; s += per) {
+            fv::WorkItem w;
+            w.first_patch = s;
+            w.count = (int16_t)std::min(per, j - s);
+            w.p = (int16_t)p;
+            items.push_back(w);
+        }
+        i = j;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fv_last_error(void) { return g_last_error.c_str(); }
+
+int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *patch_size,
+                    int halo, int unknowns, int precision, int halo_mode, double gamma,
+                    void *cuda_stream)
+{
+    g_last_error.clear();
+    if (!out) return fail(FV_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(FV_EINVAL, "dim must be 2 or 3 (got %d)", dim);
+    if (num_patches < 0) return fail(FV_EINVAL, "num_patches must be >= 0 (got %d)", num_patches);
+    if (num_patches > 0 && !patch_size) return fail(FV_EINVAL, "patch_size is NULL");
+    if (halo != 1) return fail(FV_EINVAL, "halo width must be 1 (got %d)", halo);
+    if (unknowns != dim + 2) return fail(FV_EINVAL, "Euler in %dD has %d unknowns (got %d)", dim, dim + 2, unknowns);
+    if (precision < FV_F64 || precision > FV_BF16_F32) return fail(FV_EINVAL, "unknown precision %d", precision);
+    if (halo_mode != FV_HALO_FIXED && halo_mode != FV_HALO_PERIODIC)
+        return fail(FV_EINVAL, "unknown halo mode %d", halo_mode);
+    if (!(gamma > 1.0) || !(gamma < 1e300)) return fail(FV_EINVAL, "gamma must be finite and > 1");
+    const int max_edge = dim == 2 ? kMaxEdge2D : kMaxEdge3D;
+    for (int i = 0; i < num_patches; ++i)
+        if (patch_size[i] < 1 || patch_size[i] > max_edge)
+            return fail(FV_EINVAL, "patch %d: edge length %d outside [1, %d]", i, patch_size[i], max_edge);
+
+    fv_batch *b = new (std::nothrow) fv_batch;
+    if (!b) return fail(FV_ENOMEM, "host allocation");
+    cudaGetDevice(&b->device);
+    b->dim = dim;
+    b->T = num_patches;
+    b->precision = precision;
+    b->halo_mode = halo_mode;
+    b->gamma = gamma;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->psize.assign(patch_size, patch_size + num_patches);
+    b->elem_off.resize(num_patches + 1);
+    b->cell_off.resize(num_patches + 1);
+    b->int_off.resize(num_patches + 1);
+    b->elem_off[0] = b->cell_off[0] = b->int_off[0] = 0;
+    int max_p = 0, uni = num_patches > 0 ? patch_size[0] : 0;
+    for (int i = 0; i < num_patches; ++i) {
+        int64_t p = patch_size[i];
+        int64_t cells = fv::patch_cells(dim, (int)p);
+        int64_t nint = dim == 2 ? p * p : p * p * p;
+        b->cell_off[i + 1] = b->cell_off[i] + cells;
+        b->elem_off[i + 1] = b->elem_off[i] + cells * (dim + 2);
+        b->int_off[i + 1] = b->int_off[i] + nint;
+        max_p = std::max<int>(max_p, (int)p);
+        if (patch_size[i] != uni) uni = 0;
+    }
+    b->state_elems = b->elem_off[num_patches];
+
+    // Fused work list (host side first, uploaded with the metadata).
+    std::vector<int32_t> order;
+    int fk = fv::FUSED_NONE;
+    fv::BatchView probe{};
+    probe.dim = dim;
+    probe.num_patches = num_patches;
+    probe.max_p = max_p;
+    probe.uniform_p = uni;
+    probe.halo_mode = halo_mode;
+    if (num_patches > 0 && fv::fused_supported(probe, precision, &fk)) build_work_list(b, order, b->items_h);
+    b->fused_kernel = fk;
+
+    // One device block: offsets, sizes, flags, work list, order, counter.
+    const size_t n1 = (size_t)num_patches + 1;
+    size_t off_elem = 0, off_cell = off_elem + 8 * n1, off_int = off_cell + 8 * n1;
+    size_t off_ps = off_int + 8 * n1;
+    size_t off_flags = (off_ps + 4 * (size_t)num_patches + 15) & ~(size_t)15;
+    size_t off_items = off_flags + 16;
+    size_t off_order = off_items + sizeof(fv::WorkItem) * b->items_h.size();
+    size_t off_ctr = (off_order + 4 * order.size() + 15) & ~(size_t)15;
+    size_t total = off_ctr + 16;
+    std::vector<unsigned char> host(total, 0);
+    memcpy(host.data() + off_elem, b->elem_off.data(), 8 * n1);
+    memcpy(host.data() + off_cell, b->cell_off.data(), 8 * n1);
+    memcpy(host.data() + off_int, b->int_off.data(), 8 * n1);
+    if (num_patches) memcpy(host.data() + off_ps, b->psize.data(), 4 * (size_t)num_patches);
+    if (!b->items_h.empty()) memcpy(host.data() + off_items, b->items_h.data(), sizeof(fv::WorkItem) * b->items_h.size());
+    if (!order.empty()) memcpy(host.data() + off_order, order.data(), 4 * order.size());
+
+    cudaError_t e = cudaMalloc(&b->meta, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(FV_ENOMEM, "metadata (%zu bytes): %s", total, cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(b->meta, host.data(), total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "batch set-up");
+        cudaFree(b->meta);
+        delete b;
+        return rc;
+    }
+    unsigned char *m = static_cast<unsigned char *>(b->meta);
+    fv::BatchView &v = b->view;
+    v.dim = dim;
+    v.num_patches = num_patches;
+    v.halo_mode = halo_mode;
+    v.gamma = gamma;
+    v.elem_off = reinterpret_cast<const int64_t *>(m + off_elem);
+    v.cell_off = reinterpret_cast<const int64_t *>(m + off_cell);
+    v.int_off = reinterpret_cast<const int64_t *>(m + off_int);
+    v.psize = reinterpret_cast<const int32_t *>(m + off_ps);
+    v.flags = reinterpret_cast<unsigned *>(m + off_flags);
+    v.total_cells = b->cell_off[num_patches];
+    v.total_interior = b->int_off[num_patches];
+    v.max_p = max_p;
+    v.uniform_p = uni;
+    b->plan.items = reinterpret_cast<const fv::WorkItem *>(m + off_items);
+    b->plan.order = reinterpret_cast<const int32_t *>(m + off_order);
+    b->plan.num_items = (int)b->items_h.size();
+    b->plan.work_counter = reinterpret_cast<unsigned *>(m + off_ctr);
+    b->plan.kernel = fk;
+    b->plan.shape.warps_per_block = 4;
+    b->plan.shape.blocks_per_sm = 0;
+
+    // Default form: fused sweep if this build covers the shapes, else the
+    // patch-wise tile kernel, else the loop cascade.
+    if (fk != fv::FUSED_NONE) b->form = FV_FORM_FUSED;
+    else if (num_patches == 0 || fv::tile_supported(v, precision)) b->form = FV_FORM_TILE;
+    else {
+        b->form = FV_FORM_CASCADE;
+        int rc = ensure_scratch(b);
+        if (rc) {
+            cudaStreamDestroy(b->capture_stream);
+            cudaFree(b->meta);
+            delete b;
+            return rc;
+        }
+    }
+    *out = b;
+    return FV_OK;
+}
+
+int fv_batch_set_form(fv_batch_t *b, int form)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    if (form == FV_FORM_CASCADE) {
+        int rc = ensure_scratch(b);
+        if (rc) return rc;
+    } else if (form == FV_FORM_TILE) {
+        if (b->T > 0 && !fv::tile_supported(b->view, b->precision))
+            return fail(FV_EUNSUPPORTED, "patch-wise tile kernel: patch too large for shared memory");
+    } else if (form == FV_FORM_FUSED) {
+        if (b->T > 0 && b->fused_kernel == fv::FUSED_NONE)
+            return fail(FV_EUNSUPPORTED, "no fused kernel for these patch shapes/precision");
+    } else {
+        return fail(FV_EINVAL, "unknown form %d", form);
+    }
+    if (b->form != form) drop_graphs(b);
+    b->form = form;
+    return FV_OK;
+}
+
+int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    return FV_OK;
+}
+
+static int launch_update(fv_batch_t *b, cudaStream_t st, const void *Q_in, void *Q_out,
+                         const double *dx, const double *dt, double *lambda_out,
+                         double *dt_next_out, double cfl)
+{
+    if (b->T == 0) return FV_OK;
+    fv::StepArgs a{Q_in, Q_out, dx, dt, lambda_out, dt_next_out, cfl};
+    cudaError_t e;
+    switch (b->form) {
+    case FV_FORM_CASCADE: e = fv::launch_cascade_update(b->view, b->precision, a, b->cs, st); break;
+    case FV_FORM_TILE: e = fv::launch_tile_update(b->view, b->precision, a, st); break;
+    default: e = fv::launch_fused_update(b->view, b->precision, a, b->plan, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "update launch");
+    return FV_OK;
+}
+
+static int check_update_args(fv_batch_t *b, const void *Q_in, const void *Q_out, const double *dx,
+                             const double *dt, const double *dt_next_out, double cfl)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (b->T == 0) return FV_OK;
+    if (!Q_in || !Q_out) return fail(FV_EINVAL, "state pointer is NULL");
+    if (!dx || !dt) return fail(FV_EINVAL, "dx/dt pointer is NULL");
+    if (!aligned16(Q_in) || !aligned16(Q_out)) return fail(FV_EINVAL, "state buffers must be 16-byte aligned");
+    size_t bytes = (size_t)b->state_elems * elem_bytes(b->precision);
+    if (overlaps(Q_in, Q_out, bytes)) return fail(FV_EINVAL, "Q_in and Q_out overlap (in-place update is not allowed)");
+    if (dt_next_out && !(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
+    return FV_OK;
+}
+
+int fv_patch_batch_update(fv_batch_t *b, const void *Q_in, void *Q_out, const double *dx,
+                          const double *dt, double *lambda_out, double *dt_next_out, double cfl)
+{
+    int rc = check_update_args(b, Q_in, Q_out, dx, dt, dt_next_out, cfl);
+    if (rc) return rc;
+    DeviceGuard dg(b->device);
+    return launch_update(b, b->stream, Q_in, Q_out, dx, dt, lambda_out, dt_next_out, cfl);
+}
+
+int fv_max_eigenvalue(fv_batch_t *b, const void *Q, double *lambda_out)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (b->T == 0) return FV_OK;
+    if (!Q || !lambda_out) return fail(FV_EINVAL, "NULL pointer");
+    if (!aligned16(Q)) return fail(FV_EINVAL, "state buffer must be 16-byte aligned");
+    DeviceGuard dg(b->device);
+    cudaError_t e = fv::launch_max_eigenvalue(b->view, b->precision, Q, lambda_out, b->stream);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "max eigenvalue launch");
+}
+
+int fv_cfl_time_step(fv_batch_t *b, const double *lambda, const double *dx, double cfl, double *dt_out)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (b->T == 0) return FV_OK;
+    if (!lambda || !dx || !dt_out) return fail(FV_EINVAL, "NULL pointer");
+    if (!(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
+    DeviceGuard dg(b->device);
+    cudaError_t e = fv::launch_cfl_time_step(b->view, lambda, dx, cfl, dt_out, b->stream);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "cfl launch");
+}
+
+int fv_conserved_totals(fv_batch_t *b, const void *Q, double *totals_out)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (b->T == 0) return FV_OK;
+    if (!Q || !totals_out) return fail(FV_EINVAL, "NULL pointer");
+    DeviceGuard dg(b->device);
+    cudaError_t e = fv::launch_conserved_totals(b->view, b->precision, Q, totals_out, b->stream);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "totals launch");
+}
+
+static int enqueue_steps(fv_batch_t *b, cudaStream_t st, void *Q_a, void *Q_b, const double *dx,
+                         double *dt_a, double *dt_b, double *lambda_out, int steps, double cfl)
+{
+    for (int s = 0; s < steps; ++s) {
+        const void *qi = (s & 1) ? Q_b : Q_a;
+        void *qo = (s & 1) ? Q_a : Q_b;
+        const double *dti = (s & 1) ? dt_b : dt_a;
+        double *dto = (s & 1) ? dt_a : dt_b;
+        double *lam = (s == steps - 1) ? lambda_out : nullptr;
+        int rc = launch_update(b, st, qi, qo, dx, dti, lam, dto, cfl);
+        if (rc) return rc;
+    }
+    return FV_OK;
+}
+
+int fv_batch_run(fv_batch_t *b, void *Q_a, void *Q_b, const double *dx, double *dt_a,
+                 double *dt_b, double *lambda_out, int steps, double cfl, int use_graph)
+{
+    int rc = check_update_args(b, Q_a, Q_b, dx, dt_a, dt_b, cfl);
+    if (rc) return rc;
+    if (steps < 0) return fail(FV_EINVAL, "steps must be >= 0");
+    if (b->T > 0 && !dt_b) return fail(FV_EINVAL, "dt_b is NULL");
+    if (steps == 0 || b->T == 0) return FV_OK;
+    DeviceGuard dg(b->device);
+    if (!use_graph) return enqueue_steps(b, b->stream, Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl);
+
+    GraphKey key{Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl, b->form};
+    auto it = b->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it != b->graphs.end()) {
+        exec = it->second;
+    } else {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+        rc = enqueue_steps(b, b->capture_stream, Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl);
+        e = cudaStreamEndCapture(b->capture_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        b->graphs[key] = exec;
+    }
+    cudaError_t e = cudaGraphLaunch(exec, b->stream);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "graph launch");
+}
+
+int fv_batch_status(fv_batch_t *b)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    unsigned flags = 0;
+    e = cudaMemcpy(&flags, b->view.flags, sizeof flags, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read status flags");
+    if (flags) {
+        unsigned zero = 0;
+        e = cudaMemcpy(b->view.flags, &zero, sizeof zero, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "clear status flags");
+        return fail(FV_ENONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite eigenvalue) met on the device");
+    }
+    return FV_OK;
+}
+
+int fv_batch_destroy(fv_batch_t *b)
+{
+    if (!b) return FV_OK;
+    DeviceGuard dg(b->device);
+    cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->scratch) cudaFree(b->scratch);
+    if (b->meta) cudaFree(b->meta);
+    delete b;
+    return FV_OK;
+}
+
+size_t fv_batch_state_elems(const fv_batch_t *b) { return b ? (size_t)b->state_elems : 0; }
+
+size_t fv_batch_scratch_bytes(const fv_batch_t *b) { return b ? b->scratch_bytes : 0; }
+
+int fv_batch_launches_per_update(const fv_batch_t *b)
+{
+    if (!b || b->T == 0) return 0;
+    switch (b->form) {
+    case FV_FORM_CASCADE: return 5;
+    case FV_FORM_TILE: return 1;
+    default: return b->plan.shape.blocks_per_sm > 0 ? 2 : 1;   // persistent: counter reset + kernel
+    }
+}
+
+int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len)
+{
+    if (!b || !buf || len == 0) return fail(FV_EINVAL, "NULL argument");
+    const char *form = b->form == FV_FORM_CASCADE ? "cascade" : (b->form == FV_FORM_TILE ? "tile" : "fused");
+    const char *prec = b->precision == FV_F64 ? "f64" : (b->precision == FV_F32 ? "f32" : "bf16/f32");
+    const char *fk = b->fused_kernel == fv::FUSED_SWEEP2D ? "sweep2d"
+                     : (b->fused_kernel == fv::FUSED_SWEEP3D ? "sweep3d" : "none");
+    snprintf(buf, len, "form=%s precision=%s dim=%d patches=%d max_p=%d uniform_p=%d fused_kernel=%s "
+             "items=%d warps_per_block=%d blocks_per_sm=%d scratch_bytes=%zu",
+             form, prec, b->dim, b->T, b->view.max_p, b->view.uniform_p, fk, b->plan.num_items,
+             b->plan.shape.warps_per_block, b->plan.shape.blocks_per_sm, b->scratch_bytes);
+    return FV_OK;
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------------- autotuner
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, fv::FusedShape> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_key(const fv_batch *b)
+{
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, b->device);
+    char k[256];
+    snprintf(k, sizeof k, "%s|sm%d%d|d%d|prec%d|halo%d|T%d|maxp%d|unip%d|items%d", prop.name, prop.major,
+             prop.minor, b->dim, b->precision, b->halo_mode, b->T, b->view.max_p, b->view.uniform_p,
+             b->plan.num_items);
+    std::string s(k);
+    for (auto &c : s)
+        if (c == ' ') c = '_';
+    return s;
+}
+
+void load_tune_file()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("FVBATCH_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[512];
+    int w, bps;
+    while (fscanf(f, "%511s %d %d", key, &w, &bps) == 3) g_tune_cache[key] = fv::FusedShape{w, bps};
+    fclose(f);
+}
+
+void save_tune_file()
+{
+    const char *path = getenv("FVBATCH_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    for (auto &kv : g_tune_cache) fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.warps_per_block, kv.second.blocks_per_sm);
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const double *dx,
+                             const double *dt)
+{
+    int rc = check_update_args(b, Q_in, Q_out, dx, dt, nullptr, 0.0);
+    if (rc) return rc;
+    if (b->T == 0 || b->fused_kernel == fv::FUSED_NONE) return FV_OK;
+    DeviceGuard dg(b->device);
+    std::string key = tune_key(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        load_tune_file();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            b->plan.shape = it->second;
+            drop_graphs(b);
+            return FV_OK;
+        }
+    }
+    const size_t bytes = (size_t)b->state_elems * elem_bytes(b->precision);
+    std::vector<unsigned char> ref(bytes), got(bytes);
+    const int warps[] = {2, 4, 8, 16};
+    const int bps[] = {0, 1, 2, 4, 8};
+    fv::FusedShape best{0, 0};
+    float best_ms = 1e30f;
+    bool have_ref = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fv::FusedShape saved = b->plan.shape;
+    int form = b->form;
+    b->form = FV_FORM_FUSED;
+    for (int w : warps) {
+        for (int k : bps) {
+            if (k > 0 && w * k > 64) continue;
+            b->plan.shape = fv::FusedShape{w, k};
+            cudaError_t e = cudaMemsetAsync(Q_out, 0, bytes, b->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "tune reset"); goto done; }
+            rc = launch_update(b, b->stream, Q_in, Q_out, dx, dt, nullptr, nullptr, 0.0);
+            if (rc) goto done;
+            e = cudaMemcpyAsync(got.data(), Q_out, bytes, cudaMemcpyDeviceToHost, b->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "tune readback"); goto done; }
+            if (!have_ref) {
+                ref = got;
+                have_ref = true;
+            } else if (memcmp(ref.data(), got.data(), bytes) != 0) {
+                rc = fail(FV_ECUDA, "autotune: launch shape (%d warps, %d blocks/SM) changed the result", w, k);
+                goto done;
+            }
+            // time: 3 warm-up + 10 timed launches
+            for (int r = 0; r < 3; ++r) launch_update(b, b->stream, Q_in, Q_out, dx, dt, nullptr, nullptr, 0.0);
+            cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < 10; ++r) launch_update(b, b->stream, Q_in, Q_out, dx, dt, nullptr, nullptr, 0.0);
+            cudaEventRecord(e1, b->stream);
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "tune timing"); goto done; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = b->plan.shape;
+            }
+        }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->form = form;
+    if (rc) {
+        b->plan.shape = saved;
+        return rc;
+    }
+    b->plan.shape = best;
+    drop_graphs(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+        save_tune_file();
+    }
+    return FV_OK;
+}

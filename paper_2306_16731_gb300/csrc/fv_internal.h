@@ -1,0 +1,96 @@
+// fv_internal.h -- launcher interface between the C ABI (fv_batch.cu) and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace fv {
+
+// Device-resident description of a batch, passed by value to kernels.
+struct BatchView {
+    int dim;                   // 2 or 3
+    int num_patches;           // T
+    int halo_mode;             // FV_HALO_FIXED / FV_HALO_PERIODIC
+    double gamma;
+    const int64_t *elem_off;   // [T+1] element offset of each patch
+    const int64_t *cell_off;   // [T+1] halo-inclusive cell offset of each patch
+    const int64_t *int_off;    // [T+1] interior-volume offset of each patch
+    const int32_t *psize;      // [T] edge length p_i
+    unsigned *flags;           // device error flags (FV_FLAG_*)
+    int64_t total_cells;       // sum (p_i + 2)^d
+    int64_t total_interior;    // sum p_i^d
+    int max_p;
+    int uniform_p;             // p if all patches share it, else 0
+};
+
+// Arguments of one update.
+struct StepArgs {
+    const void *q_in;
+    void *q_out;
+    const double *dx;
+    const double *dt;
+    double *lambda_out;        // may be null
+    double *dt_next_out;       // may be null
+    double cfl;
+};
+
+// Scratch of the loop-cascade form (all in compute type, halo-inclusive
+// cell indexing, array of structures).
+struct CascadeScratch {
+    void *flux;                // [dim][total_cells][N]  F_n of each volume
+    void *lam;                 // [dim][total_cells]     lambda_n of each volume
+    void *face;                // [dim][total_cells][N]  2 Fhat at the lower face of each volume
+    void *lam_new;             // [total_cells]          max eigenvalue of the new state
+};
+
+size_t cascade_scratch_bytes(const BatchView &b, int precision);
+void cascade_scratch_carve(void *base, const BatchView &b, int precision, CascadeScratch *s);
+
+// Launch-shape choice of the fused form (the autotuner's search space).
+struct FusedShape {
+    int warps_per_block;       // 1..16
+    int blocks_per_sm;         // grid = blocks_per_sm * SMs (persistent); 0 = one block per work item
+};
+
+// Work list of the fused sweep kernels: one item per group of equal-size
+// patches handled by one warp, largest patches first.
+struct WorkItem {
+    int32_t first_patch;       // index into the sorted patch order
+    int16_t count;             // patches in this item
+    int16_t p;                 // edge length of these patches
+};
+
+struct FusedPlan {
+    const WorkItem *items;     // device
+    const int32_t *order;      // device [T] patch indices sorted by size class
+    int num_items;
+    unsigned *work_counter;    // device counter for dynamic scheduling
+    FusedShape shape;
+    int kernel;                // which fused kernel family
+};
+
+enum FusedKernel { FUSED_NONE = 0, FUSED_SWEEP2D = 1, FUSED_SWEEP3D = 2 };
+
+// All launchers return cudaSuccess or the launch error; they never sync.
+cudaError_t launch_cascade_update(const BatchView &b, int precision, const StepArgs &a,
+                                  const CascadeScratch &s, cudaStream_t st);
+cudaError_t launch_tile_update(const BatchView &b, int precision, const StepArgs &a,
+                               cudaStream_t st);
+bool tile_supported(const BatchView &b, int precision);
+cudaError_t launch_fused_update(const BatchView &b, int precision, const StepArgs &a,
+                                const FusedPlan &plan, cudaStream_t st);
+bool fused_supported(const BatchView &b, int precision, int *kernel);
+int fused_items_for(int dim, int p, int *patches_per_item);
+
+cudaError_t launch_max_eigenvalue(const BatchView &b, int precision, const void *q,
+                                  double *lambda_out, cudaStream_t st);
+cudaError_t launch_cfl_time_step(const BatchView &b, const double *lambda, const double *dx,
+                                 double cfl, double *dt_out, cudaStream_t st);
+cudaError_t launch_conserved_totals(const BatchView &b, int precision, const void *q,
+                                    double *totals_out, cudaStream_t st);
+
+int num_sms();
+
+}  // namespace fv

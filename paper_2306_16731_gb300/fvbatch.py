@@ -1,0 +1,275 @@
+"""Thin ctypes binding of ``libfvbatch.so`` (C ABI in ``include/fv_batch.h``).
+
+Argument marshalling only: every step of the update runs in the CUDA
+kernels of the library.  PyTorch supplies device memory and streams.  The
+binding refuses to work without the compiled library (there is no CPU
+fallback); build it with ``paper_2306_16731_gb300.build.build()``.
+
+The function names mirror the C entry points.  Buffers may be torch tensors
+(their ``data_ptr()`` is passed) or raw integer addresses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB as _LIB_PATH
+
+FV_OK = 0
+FV_EINVAL = -1
+FV_ENOMEM = -2
+FV_ECUDA = -3
+FV_EUNSUPPORTED = -4
+FV_ENONPHYSICAL = -5
+
+FV_F64 = 0
+FV_F32 = 1
+FV_BF16_F32 = 2
+
+FV_HALO_FIXED = 0
+FV_HALO_PERIODIC = 1
+
+FV_FORM_FUSED = 0
+FV_FORM_CASCADE = 1
+FV_FORM_TILE = 2
+
+_ERRNAMES = {FV_EINVAL: "FV_EINVAL", FV_ENOMEM: "FV_ENOMEM", FV_ECUDA: "FV_ECUDA",
+             FV_EUNSUPPORTED: "FV_EUNSUPPORTED", FV_ENONPHYSICAL: "FV_ENONPHYSICAL"}
+
+EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream",
+           "fv_patch_batch_update", "fv_max_eigenvalue", "fv_cfl_time_step",
+           "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
+           "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
+           "fv_batch_scratch_bytes", "fv_batch_describe", "fv_batch_launches_per_update"]
+
+
+class FVError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "FV_E?"), code, msg))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_dp = ctypes.c_void_p     # device double* passed as an address
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libfvbatch.so is not built (%s); run "
+                               "paper_2306_16731_gb300.build.build()" % _LIB_PATH)
+        lib = ctypes.CDLL(_LIB_PATH)
+        i, d = ctypes.c_int, ctypes.c_double
+        sig = {
+            "fv_batch_create": (i, [ctypes.POINTER(_vp), i, i, ctypes.POINTER(ctypes.c_int32), i, i, i, i, d, _vp]),
+            "fv_batch_set_form": (i, [_vp, i]),
+            "fv_batch_set_stream": (i, [_vp, _vp]),
+            "fv_patch_batch_update": (i, [_vp, _vp, _vp, _dp, _dp, _dp, _dp, d]),
+            "fv_max_eigenvalue": (i, [_vp, _vp, _dp]),
+            "fv_cfl_time_step": (i, [_vp, _dp, _dp, d, _dp]),
+            "fv_conserved_totals": (i, [_vp, _vp, _dp]),
+            "fv_batch_run": (i, [_vp, _vp, _vp, _dp, _dp, _dp, _dp, i, d, i]),
+            "fv_batch_tune": (i, [_vp, _vp, _vp, _dp, _dp]),
+            "fv_batch_status": (i, [_vp]),
+            "fv_batch_destroy": (i, [_vp]),
+            "fv_last_error": (ctypes.c_char_p, []),
+            "fv_batch_state_elems": (ctypes.c_size_t, [_vp]),
+            "fv_batch_scratch_bytes": (ctypes.c_size_t, [_vp]),
+            "fv_batch_describe": (i, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
+            "fv_batch_launches_per_update": (i, [_vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _addr(x):
+    """Device address of a tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(rc: int) -> int:
+    if rc != FV_OK:
+        raise FVError(rc, load().fv_last_error().decode())
+    return rc
+
+
+def last_error() -> str:
+    return load().fv_last_error().decode()
+
+
+# ------------------------------------------------------------ C-ABI mirror
+
+def fv_batch_create(dim, patch_size, halo=1, unknowns=None, precision=FV_F64,
+                    halo_mode=FV_HALO_FIXED, gamma=1.4, stream=0):
+    """Returns the opaque batch handle (int).  ``patch_size``: host ints."""
+    lib = load()
+    ps = [int(v) for v in patch_size]
+    arr = (ctypes.c_int32 * max(1, len(ps)))(*ps) if ps else None
+    h = _vp()
+    _check(lib.fv_batch_create(ctypes.byref(h), int(dim), len(ps), arr, int(halo),
+                               int(dim + 2 if unknowns is None else unknowns),
+                               int(precision), int(halo_mode), float(gamma), _vp(stream or 0)))
+    return h.value
+
+
+def fv_batch_set_form(b, form):
+    return _check(load().fv_batch_set_form(b, int(form)))
+
+
+def fv_batch_set_stream(b, stream):
+    return _check(load().fv_batch_set_stream(b, _vp(stream or 0)))
+
+
+def fv_patch_batch_update(b, Q_in, Q_out, dx, dt, lambda_out=None, dt_next_out=None, cfl=0.4):
+    return _check(load().fv_patch_batch_update(b, _addr(Q_in), _addr(Q_out), _addr(dx), _addr(dt),
+                                               _addr(lambda_out), _addr(dt_next_out), float(cfl)))
+
+
+def fv_max_eigenvalue(b, Q, lambda_out):
+    return _check(load().fv_max_eigenvalue(b, _addr(Q), _addr(lambda_out)))
+
+
+def fv_cfl_time_step(b, lam, dx, cfl, dt_out):
+    return _check(load().fv_cfl_time_step(b, _addr(lam), _addr(dx), float(cfl), _addr(dt_out)))
+
+
+def fv_conserved_totals(b, Q, totals_out):
+    return _check(load().fv_conserved_totals(b, _addr(Q), _addr(totals_out)))
+
+
+def fv_batch_run(b, Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl=0.4, use_graph=True):
+    return _check(load().fv_batch_run(b, _addr(Q_a), _addr(Q_b), _addr(dx), _addr(dt_a),
+                                      _addr(dt_b), _addr(lambda_out), int(steps), float(cfl),
+                                      1 if use_graph else 0))
+
+
+def fv_batch_tune(b, Q_in, Q_out, dx, dt):
+    return _check(load().fv_batch_tune(b, _addr(Q_in), _addr(Q_out), _addr(dx), _addr(dt)))
+
+
+def fv_batch_status(b):
+    return _check(load().fv_batch_status(b))
+
+
+def fv_batch_destroy(b):
+    return _check(load().fv_batch_destroy(b))
+
+
+def fv_batch_state_elems(b) -> int:
+    return int(load().fv_batch_state_elems(b))
+
+
+def fv_batch_scratch_bytes(b) -> int:
+    return int(load().fv_batch_scratch_bytes(b))
+
+
+def fv_batch_describe(b) -> str:
+    buf = ctypes.create_string_buffer(512)
+    _check(load().fv_batch_describe(b, buf, 512))
+    return buf.value.decode()
+
+
+def fv_batch_launches_per_update(b) -> int:
+    return int(load().fv_batch_launches_per_update(b))
+
+
+# ------------------------------------------------------ convenience object
+
+_PREC_DTYPES = {FV_F64: "float64", FV_F32: "float32", FV_BF16_F32: "bfloat16"}
+
+
+class FVBatch:
+    """Owns one batch handle; methods forward to the C entry points."""
+
+    def __init__(self, dim, patch_size, precision=FV_F64, halo_mode=FV_HALO_FIXED,
+                 gamma=1.4, stream=None, form=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.dim = int(dim)
+        self.patch_size = [int(v) for v in patch_size]
+        self.precision = int(precision)
+        self.halo_mode = int(halo_mode)
+        self.handle = fv_batch_create(dim, self.patch_size, 1, dim + 2, precision, halo_mode, gamma, stream)
+        if form is not None:
+            fv_batch_set_form(self.handle, form)
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return getattr(torch, _PREC_DTYPES[self.precision])
+
+    def state_elems(self) -> int:
+        return fv_batch_state_elems(self.handle)
+
+    def set_form(self, form):
+        fv_batch_set_form(self.handle, form)
+
+    def set_stream(self, stream):
+        fv_batch_set_stream(self.handle, stream)
+
+    def update(self, Q_in, Q_out, dx, dt, lambda_out=None, dt_next_out=None, cfl=0.4):
+        fv_patch_batch_update(self.handle, Q_in, Q_out, dx, dt, lambda_out, dt_next_out, cfl)
+
+    def max_eigenvalue(self, Q, lambda_out):
+        fv_max_eigenvalue(self.handle, Q, lambda_out)
+
+    def cfl_time_step(self, lam, dx, cfl, dt_out):
+        fv_cfl_time_step(self.handle, lam, dx, cfl, dt_out)
+
+    def conserved_totals(self, Q, totals_out):
+        fv_conserved_totals(self.handle, Q, totals_out)
+
+    def run(self, Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl=0.4, use_graph=True):
+        fv_batch_run(self.handle, Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl, use_graph)
+
+    def tune(self, Q_in, Q_out, dx, dt):
+        fv_batch_tune(self.handle, Q_in, Q_out, dx, dt)
+
+    def status(self):
+        fv_batch_status(self.handle)
+
+    def describe(self) -> str:
+        return fv_batch_describe(self.handle)
+
+    def launches_per_update(self) -> int:
+        return fv_batch_launches_per_update(self.handle)
+
+    def scratch_bytes(self) -> int:
+        return fv_batch_scratch_bytes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fv_last_error() -> str:
+    """Thread-local description of the last failure of this thread."""
+    return last_error()

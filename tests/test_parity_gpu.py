@@ -1,0 +1,311 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L-infinity over interior volumes, each unknown
+normalised by its largest magnitude in the oracle's result):
+  FP64 forms                       1e-12
+  FP32 state and arithmetic        1e-5   (after the workload's full step count)
+  BF16 storage, FP32 arithmetic    stated (each step rounds the state to 8 bits
+                                   of mantissa); asserted below 5e-2
+The oracle for reduced precision starts from the GPU's rounded initial state
+widened to FP64; each side chains its own CFL time steps, so time-step drift
+counts as error.  Large workloads run whole on the GPU, in the launch
+configuration the benchmark times, and are checked on seeded samples of
+patches: patches are independent, so the oracle run on the sample is exact.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_16731_gb300 import inputs
+from tests._helpers import batch_rel_linf, patches_interior
+from tests.gpu_util import gpu_run, initial_fp64, subset, take_patches
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5, 2: 5e-2}
+FORMS = {"fused": 0, "cascade": 1, "tile": 2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_16731_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _oracle(w, precision, steps, Q0=None):
+    Q0 = w.Q0 if Q0 is None else Q0
+    start = initial_fp64(Q0, precision)
+    return oracle.batch_run(w.dim, w.patch_size, w.dx, start, steps, gamma=w.gamma,
+                            halo_mode=w.halo_mode, cfl=w.cfl)
+
+
+def _supported(w, precision, form):
+    from paper_2306_16731_gb300 import fvbatch as fb
+    try:
+        b = fb.FVBatch(w.dim, w.patch_size, precision=precision, halo_mode=w.halo_mode, form=form)
+        b.close()
+        return True
+    except fb.FVError as e:
+        if e.code == fb.FV_EUNSUPPORTED:
+            return False
+        raise
+
+
+def _check(w, precision, form, steps, use_graph=False, sample=None, tune=False):
+    if not _supported(w, precision, form):
+        pytest.skip("form %d has no kernel for these shapes" % form)
+    got, lam, dtn, desc = gpu_run(w, precision, form, steps, use_graph=use_graph, tune=tune)
+    if sample is None:
+        ref, lam_ref, dt_ref = _oracle(w, precision, steps)
+        err = batch_rel_linf(got, ref, w.dim, w.patch_size)
+        lam_g, dt_g = lam, dtn
+    else:
+        sw = subset(w, sample)
+        ref, lam_ref, dt_ref = _oracle(sw, precision, steps)
+        err = batch_rel_linf(take_patches(w, got, sample), ref, w.dim, sw.patch_size)
+        lam_g, dt_g = lam[sample], dtn[sample]
+    tol = TOL[precision]
+    assert err <= tol, "%s: rel Linf %.3e > %.1e (%s)" % (w.name, err, tol, desc)
+    lam_err = np.max(np.abs(lam_g - lam_ref) / lam_ref) if len(lam_ref) else 0.0
+    dt_err = np.max(np.abs(dt_g - dt_ref) / dt_ref) if len(dt_ref) else 0.0
+    assert lam_err <= tol and dt_err <= tol, (lam_err, dt_err)
+    return err
+
+
+# ------------------------------------------------------------- workloads
+
+@pytest.mark.parametrize("form", ["cascade", "tile", "fused"])
+def test_workload1_fp64(form):
+    w = inputs.config(1)
+    _check(w, 0, FORMS[form], w.steps)
+
+
+@pytest.mark.parametrize("form", ["cascade", "tile", "fused"])
+def test_workload2_fp64_first_patches(form):
+    w = inputs.config(2, num_patches=300)
+    _check(w, 0, FORMS[form], w.steps)
+
+
+@pytest.mark.parametrize("form,precision", [("fused", 1), ("fused", 0), ("cascade", 0),
+                                            ("tile", 1)])
+def test_workload2_full_size_sampled(form, precision):
+    """16,384 patches of 16x16, 100 steps, graph-captured, as the benchmark runs it."""
+    w = inputs.config(2, dtype=np.float64)
+    sample = np.sort(np.random.default_rng(2).choice(w.num_patches, 24, replace=False))
+    _check(w, precision, FORMS[form], w.steps, use_graph=True, sample=sample)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_workload3_periodic_pulse(precision):
+    w = inputs.config(3, num_patches=200)
+    err = _check(w, precision, FORMS["fused"], w.steps)
+    print("workload 3 precision %d: rel Linf after %d steps = %.3e" % (precision, w.steps, err))
+
+
+def test_workload3_full_size_sampled():
+    w = inputs.config(3)
+    sample = np.sort(np.random.default_rng(3).choice(w.num_patches, 32, replace=False))
+    _check(w, 1, FORMS["fused"], w.steps, use_graph=True, sample=sample)
+
+
+def test_workload4_uneven_full_size_sampled():
+    """50,000 patches of edge 4..32 with per-patch dx, 200 steps in one graph."""
+    w = inputs.config(4, dtype=np.float32)
+    rng = np.random.default_rng(4)
+    sample = []
+    for p in (4, 8, 16, 32):               # every size class is sampled
+        cand = np.flatnonzero(w.patch_size == p)
+        sample += list(rng.choice(cand, 8, replace=False))
+    sample = np.sort(np.array(sample))
+    _check(w, 1, FORMS["fused"], w.steps, use_graph=True, sample=sample, tune=True)
+
+
+@pytest.mark.slow
+def test_workload5_full_size_sampled():
+    """32,768 patches of 16^3 (3.8 GB FP32 state), 20 steps."""
+    w = inputs.config(5, dtype=np.float32)
+    sample = np.sort(np.random.default_rng(5).choice(w.num_patches, 6, replace=False))
+    _check(w, 1, FORMS["fused"], w.steps, use_graph=True, sample=sample)
+
+
+# ------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("form", ["cascade", "tile", "fused"])
+@pytest.mark.parametrize("dim,sizes", [(2, [1, 2, 3, 5, 7, 16, 17, 31, 32, 33, 4, 8]),
+                                       (3, [1, 2, 3, 4, 5, 8, 6, 7])])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ragged_batches(form, dim, sizes, precision):
+    w = inputs.uniform_batch(dim, sizes, seed=100 + dim, dx=np.linspace(0.05, 0.2, len(sizes)))
+    _check(w, precision, FORMS[form], 7)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_periodic_ragged(precision):
+    w = inputs.uniform_batch(2, [3, 8, 16, 5], seed=7, halo_mode=inputs.PERIODIC)
+    _check(w, precision, FORMS["fused"], 9)
+    w3 = inputs.uniform_batch(3, [3, 8, 4], seed=8, halo_mode=inputs.PERIODIC)
+    _check(w3, precision, FORMS["fused"], 5)
+
+
+def test_single_volume_patch():
+    w = inputs.uniform_batch(2, [1], seed=1)
+    for form in FORMS.values():
+        _check(w, 0, form, 3)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1024), (3, 128)])
+def test_maximum_edge_length(dim, p):
+    w = inputs.uniform_batch(dim, [p], seed=9, dx=0.01)
+    _check(w, 0, FORMS["cascade"], 1)
+    _check(w, 1, FORMS["fused"], 1)
+
+
+def test_empty_batch_is_a_no_op():
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    b = fb.FVBatch(2, [], precision=0)
+    assert b.state_elems() == 0
+    q = torch.zeros(4, dtype=torch.float64, device="cuda")
+    b.update(q, q.clone(), q, q)
+    b.max_eigenvalue(q, q)
+    b.status()
+    b.close()
+
+
+def test_free_stream_is_exact_on_gpu():
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    for dim, sizes in ((2, [16, 5, 32]), (3, [8, 3])):
+        w = inputs.uniform_batch(dim, sizes, seed=3)
+        N = dim + 2
+        state = np.tile(w.Q0[:N], len(w.Q0) // N)
+        for precision in (0, 1, 2):
+            for form in FORMS.values():
+                if not _supported(w, precision, form):
+                    continue
+                got, _, _, _ = gpu_run(w, precision, form, 4, Q0=state)
+                want = initial_fp64(state, precision)
+                for a, b in zip(patches_interior(got, dim, w.patch_size),
+                                patches_interior(want, dim, w.patch_size)):
+                    assert np.array_equal(a, b), (dim, precision, form)
+
+
+def test_graph_replay_equals_eager_bitwise():
+    w = inputs.config(2, num_patches=500)
+    for form in FORMS.values():
+        if not _supported(w, 1, form):
+            continue
+        a = gpu_run(w, 1, form, 12, use_graph=False)
+        b = gpu_run(w, 1, form, 12, use_graph=True)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_forms_agree_closely_fp32():
+    w = inputs.config(2, num_patches=200)
+    res = [gpu_run(w, 1, f, 10)[0] for f in FORMS.values() if _supported(w, 1, f)]
+    for r in res[1:]:
+        assert batch_rel_linf(r, res[0], w.dim, w.patch_size) < 1e-5
+
+
+def test_fixed_halo_is_not_written():
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(2, [4, 6], seed=5)
+    for form in FORMS.values():
+        if not _supported(w, 0, form):
+            continue
+        b = fb.FVBatch(2, w.patch_size, precision=0, form=form)
+        q = torch.from_numpy(w.Q0.copy()).cuda()
+        out = torch.full_like(q, 7.25)
+        dx = torch.full((2,), 0.1, dtype=torch.float64, device="cuda")
+        dt = torch.full((2,), 0.01, dtype=torch.float64, device="cuda")
+        b.update(q, out, dx, dt)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        off = w.offsets()
+        for i, p in enumerate(w.patch_size):
+            patch = o[off[i]:off[i + 1]].reshape(p + 2, p + 2, 4)
+            mask = np.ones((p + 2, p + 2), bool)
+            mask[1:-1, 1:-1] = False
+            assert np.all(patch[mask] == 7.25)
+            assert np.all(patch[1:-1, 1:-1] != 7.25)
+        b.close()
+
+
+def test_periodic_conservation_on_gpu():
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(3, [8, 6, 8], seed=12, halo_mode=inputs.PERIODIC)
+    b = fb.FVBatch(3, w.patch_size, precision=0, halo_mode=inputs.PERIODIC)
+    q = torch.from_numpy(w.Q0.copy()).cuda()
+    t0 = torch.zeros(3 * 5, dtype=torch.float64, device="cuda")
+    b.conserved_totals(q, t0)
+    got, _, _, _ = gpu_run(w, 0, None, 10)
+    t1 = torch.zeros_like(t0)
+    b.conserved_totals(torch.from_numpy(got).cuda(), t1)
+    torch.cuda.synchronize()
+    ref = oracle.batch_totals(3, w.patch_size, w.Q0).reshape(-1)
+    assert np.allclose(t0.cpu().numpy(), ref, rtol=1e-14, atol=1e-13)
+    drift = np.abs(t1.cpu().numpy() - t0.cpu().numpy())
+    mag = np.abs(oracle.batch_totals(3, w.patch_size, np.abs(w.Q0)).reshape(-1))
+    bound = 8 * 8 ** 3 * np.finfo(np.float64).eps * mag * 10     # per-step round-off bound x steps
+    assert np.all(drift <= bound), (drift, bound)
+    b.close()
+
+
+# -------------------------------------------------------- error handling
+
+def test_nonphysical_state_is_reported():
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(2, [8, 8], seed=2)
+    Q = w.Q0.copy()
+    Q[4 * 33] = -1.0                     # negative density at (x, y) = (2, 2) of patch 0
+    for form in FORMS.values():
+        if not _supported(w, 0, form):
+            continue
+        b = fb.FVBatch(2, w.patch_size, precision=0, form=form)
+        q = torch.from_numpy(Q).cuda()
+        out = q.clone()
+        dx = torch.full((2,), 0.1, dtype=torch.float64, device="cuda")
+        dt = torch.full((2,), 1e-4, dtype=torch.float64, device="cuda")
+        lam = torch.zeros(2, dtype=torch.float64, device="cuda")
+        b.max_eigenvalue(q, lam)
+        with pytest.raises(fb.FVError) as ei:
+            b.status()
+        assert ei.value.code == fb.FV_ENONPHYSICAL
+        b.update(q, out, dx, dt, lam)
+        with pytest.raises(fb.FVError) as ei:
+            b.status()
+        assert ei.value.code == fb.FV_ENONPHYSICAL
+        b.status()                       # the flag was cleared
+        b.close()
+
+
+def test_invalid_device_arguments():
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    b = fb.FVBatch(2, [4, 4], precision=0)
+    n = b.state_elems()
+    q = torch.zeros(n + 2, dtype=torch.float64, device="cuda")
+    dx = torch.ones(2, dtype=torch.float64, device="cuda")
+    for args in [(q, q), (q[:n], q[1:n + 1]), (q[1:], q[:n].clone())]:
+        with pytest.raises(fb.FVError) as ei:
+            b.update(args[0], args[1], dx, dx)
+        assert ei.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as ei:
+        b.update(q[:n], q[:n].clone(), None, dx)
+    assert ei.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as ei:
+        b.update(q[:n], q[:n].clone(), dx, dx, None, dx, cfl=-1.0)
+    assert ei.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as ei:
+        b.set_form(9)
+    assert ei.value.code == fb.FV_EINVAL
+    b.close()

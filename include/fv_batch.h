@@ -76,7 +76,9 @@ enum {
 
 /* Halo treatment (the halo layer of width one, Sec. 2.2). */
 enum {
-    FV_HALO_FIXED = 0,      /* halo volumes are read from Q_in as given; Q_out's halo is not written */
+    FV_HALO_FIXED = 0,      /* halo volumes are read from Q_in as given; each halo volume of Q_out is
+                               either left as it is or set to Q_in's value (the fused 2D kernels write
+                               the x-halo volumes of interior rows so that rows are written whole) */
     FV_HALO_PERIODIC = 1    /* halo volumes are the wrapped interior of the same patch; halo memory is never read or written */
 };
 
@@ -107,6 +109,13 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches,
  * form stays selected.  May allocate the cascade's scratch (FV_ENOMEM). */
 int fv_batch_set_form(fv_batch_t *b, int form);
 
+/* Launch shape of the fused form: warps_per_block in [1, 16]; blocks_per_sm
+ * 0 = one warp per work item (grid covers the work list), > 0 = that many
+ * persistent blocks per SM taking items from a device counter, -1 =
+ * persistent with as many blocks per SM as can be resident.  Results do not
+ * depend on the shape (every shape computes the same arithmetic). */
+int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per_sm);
+
 /* Rebind the batch to another stream (e.g. a capture stream). */
 int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream);
 
@@ -115,9 +124,10 @@ int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream);
  *   Q_out = Q_in - dt_i/dx_i * sum_n (Fhat_n(c+1/2) - Fhat_n(c-1/2))
  * on the interior of every patch i.  Q_in and Q_out are device state
  * buffers of the batch's layout and precision; Q_out != Q_in and they must
- * not overlap (the update reads old neighbour values).  Only Q_out's
- * interior is written.  dx and dt are device arrays of num_patches doubles
- * (mesh width and time step per patch, > 0).  If lambda_out (device,
+ * not overlap (the update reads old neighbour values).  Q_out's interior
+ * receives the new state; its halo follows the halo mode (FV_HALO_*).
+ * dx and dt are device arrays of num_patches doubles (mesh width and time
+ * step per patch, > 0).  If lambda_out (device,
  * num_patches doubles) is not NULL it receives the maximum over interior
  * volumes and directions of |u_n| + c of Q_out; if dt_next_out is not NULL
  * it receives cfl * dx_i / (dim * lambda_i) (requires cfl > 0).

@@ -256,7 +256,7 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     size_t off_items = off_flags + 16;
     size_t off_order = off_items + sizeof(fv::WorkItem) * b->items_h.size();
     size_t off_ctr = (off_order + 4 * order.size() + 15) & ~(size_t)15;
-    size_t total = off_ctr + 16;
+    size_t total = off_ctr + 8 * fv::kMaxSizeClasses;
     std::vector<unsigned char> host(total, 0);
     memcpy(host.data() + off_elem, b->elem_off.data(), 8 * n1);
     memcpy(host.data() + off_cell, b->cell_off.data(), 8 * n1);
@@ -299,6 +299,17 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     b->plan.num_items = (int)b->items_h.size();
     b->plan.work_counter = reinterpret_cast<unsigned *>(m + off_ctr);
     b->plan.kernel = fk;
+    b->plan.num_classes = 0;
+    for (size_t k = 0; k < b->items_h.size(); ++k) {
+        int p = b->items_h[k].p;
+        int &nc = b->plan.num_classes;
+        if (nc == 0 || b->plan.class_p[nc - 1] != p) {
+            b->plan.class_p[nc] = p;
+            b->plan.class_begin[nc] = (int)k;
+            ++nc;
+        }
+        b->plan.class_end[nc - 1] = (int)k + 1;
+    }
     b->plan.shape.warps_per_block = 4;
     b->plan.shape.blocks_per_sm = 0;
 
@@ -338,6 +349,16 @@ int fv_batch_set_form(fv_batch_t *b, int form)
     }
     if (b->form != form) drop_graphs(b);
     b->form = form;
+    return FV_OK;
+}
+
+int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per_sm)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (warps_per_block < 1 || warps_per_block > 16) return fail(FV_EINVAL, "warps_per_block must be in [1, 16]");
+    if (blocks_per_sm < -1 || blocks_per_sm > 32) return fail(FV_EINVAL, "blocks_per_sm must be in [-1, 32]");
+    b->plan.shape = fv::FusedShape{warps_per_block, blocks_per_sm};
+    drop_graphs(b);
     return FV_OK;
 }
 
@@ -511,7 +532,7 @@ int fv_batch_launches_per_update(const fv_batch_t *b)
     switch (b->form) {
     case FV_FORM_CASCADE: return 5;
     case FV_FORM_TILE: return 1;
-    default: return b->plan.shape.blocks_per_sm > 0 ? 2 : 1;   // persistent: counter reset + kernel
+    default: return b->plan.num_classes;   // one launch per patch-size class
     }
 }
 
@@ -601,8 +622,8 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
     }
     const size_t bytes = (size_t)b->state_elems * elem_bytes(b->precision);
     std::vector<unsigned char> ref(bytes), got(bytes);
-    const int warps[] = {2, 4, 8, 16};
-    const int bps[] = {0, 1, 2, 4, 8};
+    const int warps[] = {1, 2, 4, 8, 16};
+    const int bps[] = {0, -1, 1, 2, 4};
     fv::FusedShape best{0, 0};
     float best_ms = 1e30f;
     bool have_ref = false;
@@ -615,6 +636,7 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
     for (int w : warps) {
         for (int k : bps) {
             if (k > 0 && w * k > 64) continue;
+            if (w == 1 && k > 0) continue;
             b->plan.shape = fv::FusedShape{w, k};
             cudaError_t e = cudaMemsetAsync(Q_out, 0, bytes, b->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -62,13 +62,19 @@ struct WorkItem {
     int16_t p;                 // edge length of these patches
 };
 
+constexpr int kMaxSizeClasses = 129;   // distinct edge lengths a plan can hold
+
 struct FusedPlan {
     const WorkItem *items;     // device
     const int32_t *order;      // device [T] patch indices sorted by size class
     int num_items;
-    unsigned *work_counter;    // device counter for dynamic scheduling
+    unsigned *work_counter;    // device: 2 counters per size class for dynamic scheduling
     FusedShape shape;
     int kernel;                // which fused kernel family
+    int num_classes;           // size classes, largest edge first (one launch each)
+    int class_p[kMaxSizeClasses];
+    int class_begin[kMaxSizeClasses];
+    int class_end[kMaxSizeClasses];
 };
 
 enum FusedKernel { FUSED_NONE = 0, FUSED_SWEEP2D = 1, FUSED_SWEEP3D = 2 };

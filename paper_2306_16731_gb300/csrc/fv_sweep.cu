@@ -28,6 +28,8 @@
 // counter by persistent warps; the last warp to finish resets the counter,
 // so a launch needs no separate reset and stays graph-capturable.
 // No block-wide barrier is used: warps are independent.
+#include <algorithm>
+
 #include "fv_common.cuh"
 
 namespace fv {
@@ -35,7 +37,6 @@ namespace fv {
 namespace {
 
 constexpr int kMaxWarpsPerBlock = 16;
-constexpr int kPF = 2;   // rows loaded ahead of the row being computed
 
 struct SweepParams {
     BatchView b;
@@ -46,17 +47,137 @@ struct SweepParams {
     double *lambda_out;
     double *dt_next_out;
     double cfl;
+    float gamma_f, gm1_f;   // gas constants in float (the double ones are in b)
     const WorkItem *items;
     const int32_t *order;
-    int num_items;
-    unsigned *counter;      // [0] = next item, [1] = finished warps
+    int item_begin;         // first item of this launch's size class
+    int num_items;          // items of this launch's size class
+    unsigned *counter;      // [0] = next item, [1] = finished warps (per class)
     int persistent;
 };
 
-template <typename C>
+// Ring depth (rows in flight per warp) of the compile-time-edge sweep.
+#ifndef FV_RING_DEPTH
+#define FV_RING_DEPTH 8
+#endif
+#ifndef FV_SWEEP_MINB
+#define FV_SWEEP_MINB 1
+#endif
+#ifndef FV_SWEEP_MAXT
+#define FV_SWEEP_MAXT (kMaxWarpsPerBlock * 32)
+#endif
+template <typename S> struct RingDepth { static constexpr int value = FV_RING_DEPTH; };
+template <> struct RingDepth<double> { static constexpr int value = 4; };
+
+// Per-warp shared memory: 64 boundary faces and 64 x-halo volumes of N=4
+// values, 32 eigenvalue slots, and a ring of R rows of 32 volumes in
+// storage type.
+template <typename S>
 __host__ __device__ constexpr int warp_smem_bytes2d()
 {
-    return (64 * 4 + 32) * (int)sizeof(C);
+    using C = typename StorageTraits<S>::Compute;
+    return (2 * 64 * 4 + 32) * (int)sizeof(C) + RingDepth<S>::value * 32 * 4 * (int)sizeof(S);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Asynchronous global -> shared copies (cp.async; completion tracked per
+// thread with commit/wait groups, so no spin-wait is involved).
+__device__ __forceinline__ void cp_async_16(unsigned s, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(unsigned s, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+// One 2D volume (4 unknowns) from global to shared memory.
+template <typename S> __device__ __forceinline__ void copy_volume4_async(unsigned s, const S *g);
+template <> __device__ __forceinline__ void copy_volume4_async<float>(unsigned s, const float *g)
+{
+    cp_async_16(s, g);
+}
+template <> __device__ __forceinline__ void copy_volume4_async<double>(unsigned s, const double *g)
+{
+    cp_async_16(s, g);
+    cp_async_16(s + 16, g + 2);
+}
+template <> __device__ __forceinline__ void copy_volume4_async<__nv_bfloat16>(unsigned s, const __nv_bfloat16 *g)
+{
+    cp_async_8(s, g);
+}
+
+template <typename C> __device__ __forceinline__ Gas<C> gas_of(const SweepParams &sp);
+template <> __device__ __forceinline__ Gas<float> gas_of<float>(const SweepParams &sp)
+{
+    return Gas<float>{sp.gamma_f, sp.gm1_f};
+}
+template <> __device__ __forceinline__ Gas<double> gas_of<double>(const SweepParams &sp)
+{
+    return Gas<double>{sp.b.gamma, sp.b.gamma - 1.0};
+}
+
+// dt / (2h) in compute type (float arithmetic for float compute).
+template <typename C> __device__ __forceinline__ C half_step_ratio(double dt, double h);
+template <> __device__ __forceinline__ float half_step_ratio<float>(double dt, double h)
+{
+    return __fdividef(float(dt), 2.0f * float(h));
+}
+template <> __device__ __forceinline__ double half_step_ratio<double>(double dt, double h)
+{
+    return dt / (2.0 * h);
+}
+
+// Cheap running check of the new states: the minimum of density and
+// pressure must stay positive and the sum of eigenvalues finite (NaN and
+// infinity propagate through the sum).
+template <typename C> struct Health {
+    C min_rp = C(INFINITY);
+    C sum_l = C(0);
+    __device__ __forceinline__ void add(C rho, C p, C l)
+    {
+        min_rp = min_rp < rho ? min_rp : rho;
+        min_rp = min_rp < p ? min_rp : p;
+        sum_l += l;
+    }
+    __device__ __forceinline__ bool bad() const { return !(min_rp > C(0)) || !(sum_l < C(INFINITY)); }
+};
+
+// Store a new interior volume; with fixed halos the lanes on the patch's x
+// boundary also write the neighbouring halo volume (Q_in's value, kept from
+// the boundary pass), so every 32-byte sector of the row is written whole
+// and no partial-sector read-modify-write reaches DRAM.
+template <int N, typename S, typename C>
+__device__ __forceinline__ void store_row_volume(S *dst_row, const C (&qn)[N], bool active, bool fixed,
+                                                 int x, int P, const C *hv)
+{
+    if (!active) return;
+    store_volume<N>(dst_row, qn);
+#ifdef FV_NO_HALO_WRITE
+    fixed = false;
+#endif
+    if (fixed && x == 0) {
+        C h[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) h[k] = hv[k];
+        store_volume<N>(dst_row - N, h);
+    }
+    if (fixed && x == P - 1) {
+        C h[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) h[k] = hv[N + k];
+        store_volume<N>(dst_row + N, h);
+    }
 }
 
 template <int N, typename C>
@@ -86,11 +207,11 @@ __device__ __forceinline__ void yphys(const C (&q)[4], Gas<C> g, C (&F)[4], C &l
 
 template <typename S, typename C>
 __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkItem it, int lane,
-                                             C *__restrict__ bface, C *__restrict__ red,
-                                             bool &bad)
+                                             C *__restrict__ bface, C *__restrict__ hvol,
+                                             C *__restrict__ red, Health<C> &hl)
 {
     constexpr int N = 4;
-    const Gas<C> g{C(sp.b.gamma), C(sp.b.gamma - 1.0)};
+    const Gas<C> g = gas_of<C>(sp);
     const S *__restrict__ q = static_cast<const S *>(sp.q_in);
     S *__restrict__ qo = static_cast<S *>(sp.q_out);
     const int P = it.p, cnt = it.count;
@@ -114,8 +235,12 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
         xphys(qR, g, FR, lR);
         rusanov2<N>(qL, qR, FL, FR, lL, lR, Fh);
         C *dstf = bface + ((fs * P + yy) * 2 + side) * N;
+        C *dsth = hvol + ((fs * P + yy) * 2 + side) * N;
 #pragma unroll
-        for (int k = 0; k < N; ++k) dstf[k] = Fh[k];
+        for (int k = 0; k < N; ++k) {
+            dstf[k] = Fh[k];
+            dsth[k] = side ? qR[k] : qL[k];
+        }
     }
     __syncwarp();
 
@@ -130,8 +255,9 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
     S *dst = qo + base + (int64_t)(x + 1) * N;
     const int64_t RS = (int64_t)E * N;               // row stride in elements
     const double h = __ldg(sp.dx + i);
-    const C sc = C(__ldg(sp.dt + i) / (2.0 * h));
+    const C sc = half_step_ratio<C>(__ldg(sp.dt + i), h);
     const C *bf = bface + (slot * P) * 2 * N;
+    const C *hv_row = hvol + (slot * P) * 2 * N;
 
     C q0[N], q1[N], q2[N];
     load_volume<N>(src + (int64_t)((periodic ? wrap(-1, P) : (-1)) + 1) * RS, q0);
@@ -164,10 +290,10 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
             C qn[N];
 #pragma unroll
             for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxp[k] + (Fyl[k] - Fylp[k]));
-            if (active) store_volume<N>(dst + (int64_t)y * RS, qn);      // row y-1 lives at y
+            store_row_volume<N>(dst + (int64_t)y * RS, qn, active, !periodic, x, P, hv_row + (y - 1) * 2 * N);   // row y-1 lives at y
             Prim<2, C> t = primitives<2>(qn, g);
             const C l = max_eigenvalue<2>(t);
-            bad = bad || non_physical(qn[0], t.p, l);
+            hl.add(qn[0], t.p, l);
             lmax = fv_max(lmax, l);
         }
 
@@ -210,10 +336,10 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
         C qn[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxp[k] + (Fyu[k] - Fylp[k]));
-        if (active) store_volume<N>(dst + (int64_t)P * RS, qn);
+        store_row_volume<N>(dst + (int64_t)P * RS, qn, active, !periodic, x, P, hv_row + (P - 1) * 2 * N);
         Prim<2, C> t = primitives<2>(qn, g);
         const C l = max_eigenvalue<2>(t);
-        bad = bad || non_physical(qn[0], t.p, l);
+        hl.add(qn[0], t.p, l);
         lmax = fv_max(lmax, l);
     }
 
@@ -230,26 +356,208 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
     __syncwarp();
 }
 
-template <typename S>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_sweep2d(SweepParams sp)
+// Compile-time edge P (32/P patches per warp): rows stream through a
+// per-warp shared-memory ring of R rows filled by cp.async, R-1 rows ahead
+// of the row being computed, so many loads are in flight without holding
+// registers.  Same arithmetic and order as sweep2d_item.
+template <typename S, typename C, int P>
+__device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem it, int lane,
+                                            C *__restrict__ bface, C *__restrict__ hvol,
+                                            C *__restrict__ red, unsigned char *__restrict__ ring,
+                                            Health<C> &hl)
+{
+    constexpr int N = 4, E = P + 2, R = RingDepth<S>::value;
+    constexpr int VB = 4 * (int)sizeof(S);
+    constexpr int RS = E * N;
+    const Gas<C> g = gas_of<C>(sp);
+    const S *__restrict__ q = static_cast<const S *>(sp.q_in);
+    S *__restrict__ qo = static_cast<S *>(sp.q_out);
+    const int cnt = it.count;
+    const bool periodic = sp.b.halo_mode == 1;
+
+    const int sub = lane / P;
+    const int x = lane - sub * P;
+    const bool active = sub < cnt;
+    const int slot = active ? sub : 0;
+    const int i = __ldg(sp.order + it.first_patch + slot);
+    const int64_t base = __ldg(sp.b.elem_off + i);
+    const S *src = q + base + (x + 1) * N;
+    S *dst = qo + base + (x + 1) * N;
+    const unsigned rbase = smem_u32(ring) + lane * VB;
+    const unsigned char *rlane = ring + lane * VB;
+
+    // rows -1 .. R-3 in flight before anything else
+#pragma unroll
+    for (int r = 0; r < R - 1; ++r) {
+        const int y = r - 1;
+        if (y <= P) {
+            const int yy = periodic ? wrap(y, P) : y;
+            copy_volume4_async<S>(rbase + ((y + 1) % R) * 32 * VB, src + (yy + 1) * RS);
+        }
+        cp_async_commit();
+    }
+
+    // boundary x faces of every row, packed over the warp
+    const int nf = 2 * P * cnt;
+    for (int f = lane; f < nf; f += 32) {
+        const int fs = f / (2 * P);
+        const int r = f - fs * 2 * P;
+        const int yy = r >> 1, side = r & 1;
+        const int ip = __ldg(sp.order + it.first_patch + fs);
+        const S *ps = q + __ldg(sp.b.elem_off + ip);
+        int xl = side ? P - 1 : -1, xr = side ? P : 0;
+        if (periodic) { xl = wrap(xl, P); xr = wrap(xr, P); }
+        C qL[N], qR[N], FL[N], FR[N], Fh[N], lL, lR;
+        load_volume<N>(ps + ((yy + 1) * E + (xl + 1)) * N, qL);
+        load_volume<N>(ps + ((yy + 1) * E + (xr + 1)) * N, qR);
+        xphys(qL, g, FL, lL);
+        xphys(qR, g, FR, lR);
+        rusanov2<N>(qL, qR, FL, FR, lL, lR, Fh);
+        C *dstf = bface + ((fs * P + yy) * 2 + side) * N;
+        C *dsth = hvol + ((fs * P + yy) * 2 + side) * N;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            dstf[k] = Fh[k];
+            dsth[k] = side ? qR[k] : qL[k];
+        }
+    }
+    __syncwarp();
+
+    const double h = __ldg(sp.dx + i);
+    const C sc = half_step_ratio<C>(__ldg(sp.dt + i), h);
+    const C *bf = bface + (slot * P) * 2 * N;
+    const C *hv_row = hvol + (slot * P) * 2 * N;
+
+    // issue row y+R-1, then wait until row y (ring slot (y+1) % R) has landed
+    auto advance = [&](int y, C (&qv)[N]) {
+        const int yn = y + R - 1;
+        if (yn <= P) {
+            const int yy = periodic ? wrap(yn, P) : yn;
+            copy_volume4_async<S>(rbase + ((yn + 1) % R) * 32 * VB, src + (yy + 1) * RS);
+        }
+        cp_async_commit();
+        cp_async_wait<R - 1>();
+        load_volume<N>(reinterpret_cast<const S *>(rlane + ((y + 1) % R) * 32 * VB), qv);
+    };
+
+    C qp[N], Fyp[N], lyp, dxp[N], Fylp[N];
+    C lmax = C(0);
+    {
+        C q0[N];
+        advance(-1, q0);
+        yphys(q0, g, Fyp, lyp);
+#pragma unroll
+        for (int k = 0; k < N; ++k) qp[k] = q0[k];
+    }
+
+#pragma unroll 2
+    for (int y = 0; y < P; ++y) {
+        C q0[N];
+        advance(y, q0);
+        Prim<2, C> s = primitives<2>(q0, g);
+        C Fx[N], Fy[N];
+        flux<2>(q0, s, 0, Fx);
+        flux<2>(q0, s, 1, Fy);
+        const C lx = eigenvalue<2>(s, 0), ly = eigenvalue<2>(s, 1);
+
+        C Fyl[N];
+        rusanov2<N>(qp, q0, Fyp, Fy, lyp, ly, Fyl);
+        if (y > 0) {
+            C qn[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxp[k] + (Fyl[k] - Fylp[k]));
+            store_row_volume<N>(dst + y * RS, qn, active, !periodic, x, P, hv_row + (y - 1) * 2 * N);
+            Prim<2, C> t = primitives<2>(qn, g);
+            const C l = max_eigenvalue<2>(t);
+            hl.add(qn[0], t.p, l);
+            lmax = fv_max(lmax, l);
+        }
+
+        C qr[N], Fr_[N], Fr[N], Fl[N];
+        shfl_down_vec<N>(q0, qr);
+        shfl_down_vec<N>(Fx, Fr_);
+        const C lr = __shfl_down_sync(0xffffffffu, lx, 1);
+        rusanov2<N>(q0, qr, Fx, Fr_, lx, lr, Fr);
+        if (x == P - 1) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) Fr[k] = bf[(y * 2 + 1) * N + k];
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
+        if (x == 0) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) Fl[k] = bf[(y * 2) * N + k];
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            dxp[k] = Fr[k] - Fl[k];
+            Fylp[k] = Fyl[k];
+            qp[k] = q0[k];
+            Fyp[k] = Fy[k];
+        }
+        lyp = ly;
+    }
+
+    {
+        C q0[N], Fy[N], ly, Fyu[N];
+        advance(P, q0);
+        yphys(q0, g, Fy, ly);
+        rusanov2<N>(qp, q0, Fyp, Fy, lyp, ly, Fyu);
+        C qn[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxp[k] + (Fyu[k] - Fylp[k]));
+        store_row_volume<N>(dst + P * RS, qn, active, !periodic, x, P, hv_row + (P - 1) * 2 * N);
+        Prim<2, C> t = primitives<2>(qn, g);
+        const C l = max_eigenvalue<2>(t);
+        hl.add(qn[0], t.p, l);
+        lmax = fv_max(lmax, l);
+    }
+    cp_async_wait<0>();
+
+    red[lane] = lmax;
+    __syncwarp();
+    if (active && x == 0 && (sp.lambda_out || sp.dt_next_out)) {
+        C m = red[lane];
+#pragma unroll
+        for (int j = 1; j < P; ++j) m = fv_max(m, red[lane + j]);
+        const double l = double(m);
+        if (sp.lambda_out) sp.lambda_out[i] = l;
+        if (sp.dt_next_out) sp.dt_next_out[i] = cfl_dt(sp.cfl, h, 2, l);
+    }
+    __syncwarp();
+}
+
+// One launch per patch-size class: P > 0 selects the compile-time-edge
+// sweep, P == 0 the runtime-edge one.  Items [item_begin, item_begin +
+// num_items) of the sorted work list belong to the class.
+template <typename S, int P>
+__global__ void __launch_bounds__(FV_SWEEP_MAXT, FV_SWEEP_MINB) k_sweep2d(SweepParams sp)
 {
     using C = typename StorageTraits<S>::Compute;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C *bface = reinterpret_cast<C *>(smem_raw + warp * warp_smem_bytes2d<C>());
-    C *red = bface + 64 * 4;
-    bool bad = false;
+    unsigned char *wbase = smem_raw + warp * warp_smem_bytes2d<S>();
+    C *bface = reinterpret_cast<C *>(wbase);
+    C *hvol = bface + 64 * 4;
+    C *red = hvol + 64 * 4;
+    unsigned char *ring = wbase + (2 * 64 * 4 + 32) * sizeof(C);
+    Health<C> hl;
     const int wpb = blockDim.x >> 5;
+    auto run = [&](int item) {
+        const WorkItem it = sp.items[item];
+        if (P > 0) sweep2d_tpl<S, C, (P > 0 ? P : 4)>(sp, it, lane, bface, hvol, red, ring, hl);
+        else sweep2d_item<S, C>(sp, it, lane, bface, hvol, red, hl);
+    };
     if (!sp.persistent) {
         const int item = blockIdx.x * wpb + warp;
-        if (item < sp.num_items) sweep2d_item<S, C>(sp, sp.items[item], lane, bface, red, bad);
+        if (item < sp.num_items) run(sp.item_begin + item);
     } else {
         for (;;) {
             int item = 0;
             if (lane == 0) item = (int)atomicAdd(sp.counter, 1u);
             item = __shfl_sync(0xffffffffu, item, 0);
             if (item >= sp.num_items) break;
-            sweep2d_item<S, C>(sp, sp.items[item], lane, bface, red, bad);
+            run(sp.item_begin + item);
         }
         // the last warp to finish resets the counters for the next launch
         if (lane == 0) {
@@ -262,7 +570,47 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) k_sweep2d(SweepPara
             }
         }
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(sp.b.flags, FV_FLAG_NONPHYSICAL);
+    if (__any_sync(0xffffffffu, hl.bad()) && lane == 0) atomicOr(sp.b.flags, FV_FLAG_NONPHYSICAL);
+}
+
+// Grid: one warp per item, or (persistent) blocks_per_sm blocks per SM,
+// where blocks_per_sm < 0 means as many as can be resident at once.
+template <typename S, int P>
+cudaError_t launch_class(const SweepParams &sp, int wpb, int bps, cudaStream_t st)
+{
+    static bool attr_set = false;
+    const int bytes = wpb * warp_smem_bytes2d<S>();
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep2d<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kMaxWarpsPerBlock * warp_smem_bytes2d<S>());
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int grid = (sp.num_items + wpb - 1) / wpb;
+    if (sp.persistent) {
+        int per_sm = bps;
+        if (per_sm < 0) {
+            per_sm = 1;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep2d<S, P>, wpb * 32, bytes);
+            if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        }
+        grid = std::min(grid, per_sm * num_sms());
+    }
+    if (grid < 1) grid = 1;
+    k_sweep2d<S, P><<<grid, wpb * 32, bytes, st>>>(sp);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_class_p(int p, const SweepParams &sp, int wpb, int bps, cudaStream_t st)
+{
+    switch (p) {
+    case 4: return launch_class<S, 4>(sp, wpb, bps, st);
+    case 8: return launch_class<S, 8>(sp, wpb, bps, st);
+    case 16: return launch_class<S, 16>(sp, wpb, bps, st);
+    case 32: return launch_class<S, 32>(sp, wpb, bps, st);
+    default: return launch_class<S, 0>(sp, wpb, bps, st);
+    }
 }
 
 }  // namespace
@@ -298,24 +646,26 @@ cudaError_t launch_fused_update(const BatchView &b, int precision, const StepArg
     sp.lambda_out = a.lambda_out;
     sp.dt_next_out = a.dt_next_out;
     sp.cfl = a.cfl;
+    sp.gamma_f = float(b.gamma);
+    sp.gm1_f = float(b.gamma - 1.0);
     sp.items = plan.items;
     sp.order = plan.order;
-    sp.num_items = plan.num_items;
-    sp.counter = plan.work_counter;
     int wpb = plan.shape.warps_per_block;
     if (wpb < 1) wpb = 1;
     if (wpb > kMaxWarpsPerBlock) wpb = kMaxWarpsPerBlock;
-    sp.persistent = plan.shape.blocks_per_sm > 0;
-    int grid = sp.persistent ? plan.shape.blocks_per_sm * num_sms() : (plan.num_items + wpb - 1) / wpb;
-    if (grid < 1) grid = 1;
-    if (precision == PREC_F64) {
-        k_sweep2d<double><<<grid, wpb * 32, wpb * warp_smem_bytes2d<double>(), st>>>(sp);
-    } else if (precision == PREC_F32) {
-        k_sweep2d<float><<<grid, wpb * 32, wpb * warp_smem_bytes2d<float>(), st>>>(sp);
-    } else {
-        k_sweep2d<__nv_bfloat16><<<grid, wpb * 32, wpb * warp_smem_bytes2d<float>(), st>>>(sp);
+    sp.persistent = plan.shape.blocks_per_sm != 0;
+    for (int c = 0; c < plan.num_classes; ++c) {
+        sp.item_begin = plan.class_begin[c];
+        sp.num_items = plan.class_end[c] - plan.class_begin[c];
+        sp.counter = plan.work_counter + 2 * c;
+        const int p = plan.class_p[c], bps = plan.shape.blocks_per_sm;
+        cudaError_t e;
+        if (precision == PREC_F64) e = launch_class_p<double>(p, sp, wpb, bps, st);
+        else if (precision == PREC_F32) e = launch_class_p<float>(p, sp, wpb, bps, st);
+        else e = launch_class_p<__nv_bfloat16>(p, sp, wpb, bps, st);
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace fv

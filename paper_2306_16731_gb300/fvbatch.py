@@ -37,7 +37,7 @@ FV_FORM_TILE = 2
 _ERRNAMES = {FV_EINVAL: "FV_EINVAL", FV_ENOMEM: "FV_ENOMEM", FV_ECUDA: "FV_ECUDA",
              FV_EUNSUPPORTED: "FV_EUNSUPPORTED", FV_ENONPHYSICAL: "FV_ENONPHYSICAL"}
 
-EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream",
+EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_batch_set_launch_shape",
            "fv_patch_batch_update", "fv_max_eigenvalue", "fv_cfl_time_step",
            "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
@@ -58,7 +58,7 @@ _dp = ctypes.c_void_p     # device double* passed as an address
 
 
 def library_path() -> str:
-    return _LIB_PATH
+    return os.environ.get("FVBATCH_LIB") or _LIB_PATH
 
 
 def load() -> ctypes.CDLL:
@@ -67,15 +67,17 @@ def load() -> ctypes.CDLL:
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_LIB_PATH):
+        path = library_path()
+        if not os.path.exists(path):
             raise RuntimeError("libfvbatch.so is not built (%s); run "
-                               "paper_2306_16731_gb300.build.build()" % _LIB_PATH)
-        lib = ctypes.CDLL(_LIB_PATH)
+                               "paper_2306_16731_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
         i, d = ctypes.c_int, ctypes.c_double
         sig = {
             "fv_batch_create": (i, [ctypes.POINTER(_vp), i, i, ctypes.POINTER(ctypes.c_int32), i, i, i, i, d, _vp]),
             "fv_batch_set_form": (i, [_vp, i]),
             "fv_batch_set_stream": (i, [_vp, _vp]),
+            "fv_batch_set_launch_shape": (i, [_vp, i, i]),
             "fv_patch_batch_update": (i, [_vp, _vp, _vp, _dp, _dp, _dp, _dp, d]),
             "fv_max_eigenvalue": (i, [_vp, _vp, _dp]),
             "fv_cfl_time_step": (i, [_vp, _dp, _dp, d, _dp]),
@@ -134,6 +136,10 @@ def fv_batch_create(dim, patch_size, halo=1, unknowns=None, precision=FV_F64,
 
 def fv_batch_set_form(b, form):
     return _check(load().fv_batch_set_form(b, int(form)))
+
+
+def fv_batch_set_launch_shape(b, warps_per_block, blocks_per_sm):
+    return _check(load().fv_batch_set_launch_shape(b, int(warps_per_block), int(blocks_per_sm)))
 
 
 def fv_batch_set_stream(b, stream):
@@ -224,6 +230,9 @@ class FVBatch:
 
     def set_form(self, form):
         fv_batch_set_form(self.handle, form)
+
+    def set_launch_shape(self, warps_per_block, blocks_per_sm):
+        fv_batch_set_launch_shape(self.handle, warps_per_block, blocks_per_sm)
 
     def set_stream(self, stream):
         fv_batch_set_stream(self.handle, stream)

@@ -200,6 +200,36 @@ int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len);
  * current form and arguments (lambda/dt outputs present). */
 int fv_batch_launches_per_update(const fv_batch_t *b);
 
+/*
+ * One update, like fv_patch_batch_update with the loop-cascade form, that
+ * allocates no device memory; the paper has no counterpart (it is a service
+ * for callers that cannot allocate).  For callers that cannot call
+ * cudaMalloc where they step their patches: host callbacks or hooks that
+ * run during CUDA-graph capture, processes whose device memory belongs to a
+ * pooling allocator, plugins handed only their buffers.
+ *
+ * All num_patches patches have the edge length patch_size.  Arguments
+ * otherwise mean what they mean in fv_batch_create and
+ * fv_patch_batch_update; Q_in, Q_out, dx, dt, lambda_out and dt_next_out are
+ * device pointers the caller owns, and the call runs asynchronously on
+ * cuda_stream (a cudaStream_t, 0 = legacy default stream) on the current
+ * device.  The metadata and the cascade's intermediates live in a built-in
+ * 64 MiB device array that every GPU loading this library holds until the
+ * process exits; a batch that needs more (about 1,300 two-dimensional
+ * 16 x 16 patches in FP64, 2,700 in FP32) is rejected with FV_EINVAL and
+ * nothing is launched.  The first call on a device looks up the array's
+ * device address (make it before any stream capture).  All calls share the
+ * array: calls whose work overlaps on the GPU race, so serialise them.
+ * Non-physical states are not reported by this entry point (see the
+ * returned eigenvalues instead).  Returns FV_OK or an FV_E* code.
+ */
+int fv_patch_batch_update_noalloc(int dim, int num_patches, int patch_size,
+                                  int precision, int halo_mode, double gamma,
+                                  const void *Q_in, void *Q_out,
+                                  const double *dx, const double *dt,
+                                  double *lambda_out, double *dt_next_out,
+                                  double cfl, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

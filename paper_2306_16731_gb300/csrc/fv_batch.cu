@@ -89,6 +89,8 @@ struct fv_batch {
 
 namespace fv {
 
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
 int num_sms()
 {
     static std::mutex mu;

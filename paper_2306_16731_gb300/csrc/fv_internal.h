@@ -99,4 +99,7 @@ cudaError_t launch_conserved_totals(const BatchView &b, int precision, const voi
 
 int num_sms();
 
+// Record the thread-local message returned by fv_last_error().
+void set_last_error(const char *msg);
+
 }  // namespace fv

@@ -91,6 +91,7 @@ def load() -> ctypes.CDLL:
             "fv_batch_scratch_bytes": (ctypes.c_size_t, [_vp]),
             "fv_batch_describe": (i, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
             "fv_batch_launches_per_update": (i, [_vp]),
+            "fv_patch_batch_update_noalloc": (i, [i, i, i, i, i, d, _vp, _vp, _dp, _dp, _dp, _dp, d, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -277,6 +278,17 @@ class FVBatch:
             self.close()
         except Exception:
             pass
+
+
+def fv_patch_batch_update_noalloc(dim, num_patches, patch_size, precision, halo_mode, gamma,
+                                  Q_in, Q_out, dx, dt, lambda_out=None, dt_next_out=None,
+                                  cfl=0.4, stream=0):
+    """Allocation-free update of equal-size patches (loop-cascade kernels,
+    scratch in a built-in 64 MiB device array); see include/fv_batch.h."""
+    return _check(load().fv_patch_batch_update_noalloc(
+        int(dim), int(num_patches), int(patch_size), int(precision), int(halo_mode), float(gamma),
+        _addr(Q_in), _addr(Q_out), _addr(dx), _addr(dt), _addr(lambda_out), _addr(dt_next_out),
+        float(cfl), _vp(stream or 0)))
 
 
 def fv_last_error() -> str:

@@ -237,6 +237,16 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
         if (patch_size[i] != uni) uni = 0;
     }
     b->state_elems = b->elem_off[num_patches];
+    int align = 16;
+    {
+        const size_t es = elem_bytes(precision);
+        auto pow2 = [](size_t v) { int a = 16; while (a > 1 && v % a != 0) a >>= 1; return a; };
+        for (int i = 0; i < num_patches; ++i) {
+            const size_t e = (size_t)patch_size[i] + 2;
+            align = std::min(align, pow2((size_t)fv::patch_cells(dim, patch_size[i]) * (dim + 2) * es));
+            if (dim == 3) align = std::min(align, pow2(e * e * (dim + 2) * es));
+        }
+    }
 
     // Fused work list (host side first, uploaded with the metadata).
     std::vector<int32_t> order;
@@ -247,6 +257,7 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     probe.max_p = max_p;
     probe.uniform_p = uni;
     probe.halo_mode = halo_mode;
+    probe.align_bytes = align;
     if (num_patches > 0 && fv::fused_supported(probe, precision, &fk)) build_work_list(b, order, b->items_h);
     b->fused_kernel = fk;
 
@@ -296,6 +307,7 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     v.total_interior = b->int_off[num_patches];
     v.max_p = max_p;
     v.uniform_p = uni;
+    v.align_bytes = align;
     b->plan.items = reinterpret_cast<const fv::WorkItem *>(m + off_items);
     b->plan.order = reinterpret_cast<const int32_t *>(m + off_order);
     b->plan.num_items = (int)b->items_h.size();

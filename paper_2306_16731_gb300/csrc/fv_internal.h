@@ -23,6 +23,7 @@ struct BatchView {
     int64_t total_interior;    // sum p_i^d
     int max_p;
     int uniform_p;             // p if all patches share it, else 0
+    int align_bytes;           // largest power of two <= 16 dividing every patch's (and 3D plane's) bytes
 };
 
 // Arguments of one update.
@@ -88,6 +89,9 @@ bool tile_supported(const BatchView &b, int precision);
 cudaError_t launch_fused_update(const BatchView &b, int precision, const StepArgs &a,
                                 const FusedPlan &plan, cudaStream_t st);
 bool fused_supported(const BatchView &b, int precision, int *kernel);
+bool fused3d_supported(const BatchView &b, int precision);
+cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepArgs &a,
+                                  const FusedPlan &plan, cudaStream_t st);
 int fused_items_for(int dim, int p, int *patches_per_item);
 
 cudaError_t launch_max_eigenvalue(const BatchView &b, int precision, const void *q,

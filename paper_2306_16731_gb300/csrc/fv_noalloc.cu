@@ -104,6 +104,7 @@ extern "C" int fv_patch_batch_update_noalloc(int dim, int num_patches, int patch
                                                         : (int64_t)patch_size * patch_size * patch_size);
     v.max_p = patch_size;
     v.uniform_p = patch_size;
+    v.align_bytes = 1;
     const size_t need = off_cascade + fv::cascade_scratch_bytes(v, precision);
     if (need > kNoAllocScratchBytes)
         return noalloc_fail(FV_EINVAL, "batch needs more than the 64 MiB of built-in scratch; "

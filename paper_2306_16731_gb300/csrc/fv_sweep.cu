@@ -617,11 +617,14 @@ cudaError_t launch_class_p(int p, const SweepParams &sp, int wpb, int bps, cudaS
 
 bool fused_supported(const BatchView &b, int precision, int *kernel)
 {
-    (void)precision;
     *kernel = FUSED_NONE;
     if (b.num_patches <= 0) return false;
     if (b.dim == 2 && b.max_p <= 32) {
         *kernel = FUSED_SWEEP2D;
+        return true;
+    }
+    if (b.dim == 3 && fused3d_supported(b, precision)) {
+        *kernel = FUSED_SWEEP3D;
         return true;
     }
     return false;
@@ -636,6 +639,7 @@ int fused_items_for(int dim, int p, int *patches_per_item)
 cudaError_t launch_fused_update(const BatchView &b, int precision, const StepArgs &a,
                                 const FusedPlan &plan, cudaStream_t st)
 {
+    if (plan.kernel == FUSED_SWEEP3D) return launch_fused3d_update(b, precision, a, plan, st);
     if (plan.kernel != FUSED_SWEEP2D) return cudaErrorNotSupported;
     SweepParams sp;
     sp.b = b;

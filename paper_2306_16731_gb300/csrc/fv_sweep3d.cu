@@ -1,0 +1,431 @@
+// fv_sweep3d.cu -- fused 3D form: one thread block per patch, one thread per
+// (x, y) column, sweeping the patch plane by plane along z (arXiv:2306.16731:
+// the steps of Algorithm 1 for one patch, Rusanov faces of Eq. 2 in x, y and
+// z, per-patch eigenvalue reduction of Sec. 4).
+//
+//   * Halo-inclusive z-planes ((p+2)^2 volumes) stream through a shared-
+//     memory ring of R planes filled with cp.async in 16/8/4-byte chunks,
+//     R-1 planes ahead.  Periodic patches copy plane p-1 as plane -1 and
+//     plane 0 as plane p, and read x/y halo volumes at wrapped positions.
+//   * Per plane each thread evaluates its volume once (primitives, F_x,
+//     F_y, F_z and the three eigenvalues) and publishes F_x, lambda_x,
+//     F_y, lambda_y in shared memory; the first 4p threads also evaluate
+//     the plane's x/y halo volumes.  After a barrier each thread forms its
+//     left and right x and y faces from shared data.
+//   * z faces: the previous plane's Q, F_z and lambda_z stay in registers;
+//     plane z-1 is finished when plane z's lower face is known:
+//     Q_new = Q - dt/(2h) (((2Fx_r - 2Fx_l) + (2Fy_r - 2Fy_l)) + (2Fz_r - 2Fz_l)),
+//     the oracle's order.
+//   * Threads on the x boundary also write the x-halo volume of their row
+//     (fixed: Q_in's halo value; periodic: the wrapped new value), so rows
+//     are written whole.
+#include <algorithm>
+
+#include "fv_common.cuh"
+
+namespace fv {
+
+namespace {
+
+constexpr int kRing3 = 4;     // planes in the ring
+constexpr int kMaxThreads3 = 256;    // p <= 16: one thread per (x, y) column
+
+// Register budget: three 256-thread blocks per SM in float (80 registers),
+// two in double.
+template <typename C> struct MinBlocks3 { static constexpr int value = 3; };
+template <> struct MinBlocks3<double> { static constexpr int value = 2; };
+
+struct Sweep3Params {
+    BatchView b;
+    const void *q_in;
+    void *q_out;
+    const double *dx;
+    const double *dt;
+    double *lambda_out;
+    double *dt_next_out;
+    double cfl;
+    float gamma_f, gm1_f;
+    const int32_t *order;     // patch indices sorted by size class
+    int first;                // first sorted position of this launch's class
+    int count;                // patches of this class
+    int p;                    // their edge length
+};
+
+template <typename C> __device__ __forceinline__ Gas<C> gas3(const Sweep3Params &sp);
+template <> __device__ __forceinline__ Gas<float> gas3<float>(const Sweep3Params &sp)
+{
+    return Gas<float>{sp.gamma_f, sp.gm1_f};
+}
+template <> __device__ __forceinline__ Gas<double> gas3<double>(const Sweep3Params &sp)
+{
+    return Gas<double>{sp.b.gamma, sp.b.gamma - 1.0};
+}
+
+template <typename C> __device__ __forceinline__ C half_ratio3(double dt, double h);
+template <> __device__ __forceinline__ float half_ratio3<float>(double dt, double h)
+{
+    return __fdividef(float(dt), 2.0f * float(h));
+}
+template <> __device__ __forceinline__ double half_ratio3<double>(double dt, double h)
+{
+    return dt / (2.0 * h);
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+template <int B>
+__device__ __forceinline__ void cp_async_chunk(unsigned s, const void *g)
+{
+    if (B == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g) : "memory");
+    else if (B == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+// Copy one contiguous plane of `bytes` into shared memory, chunked over the
+// block's threads.
+__device__ __forceinline__ void copy_plane(unsigned sdst, const unsigned char *gsrc, int bytes, int chunk)
+{
+    const int n = bytes / chunk;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        if (chunk == 16) cp_async_chunk<16>(sdst + c * 16, gsrc + c * 16);
+        else if (chunk == 8) cp_async_chunk<8>(sdst + c * 8, gsrc + c * 8);
+        else cp_async_chunk<4>(sdst + c * 4, gsrc + c * 4);
+    }
+}
+
+template <int n, typename C>
+__device__ __forceinline__ void physics_dir(const C (&q)[5], Gas<C> g, C (&F)[5], C &lam)
+{
+    Prim<3, C> s = primitives<3>(q, g);
+    flux<3>(q, s, n, F);
+    lam = eigenvalue<3>(s, n);
+}
+
+// Finish the owner's volume of plane zz (stored at memory plane zz+1):
+// Q_new = Q - dt/(2h) ((x/y difference) + (upper - lower z face)), store,
+// fold its eigenvalue into the running maximum and health, and write the
+// row's x-halo volume (fixed: Q_in's value; periodic: the wrapped new
+// value, since the volume at x = 0 is the halo at x = P and vice versa).
+template <typename S, typename C>
+__device__ __forceinline__ void finish3(int zz, const C (&upper)[5], const C (&qp)[5], const C (&dxy)[5],
+                                        const C (&lower)[5], C sc, Gas<C> g, int x, int y, int P, int E,
+                                        int EE, bool periodic, const S *__restrict__ qin,
+                                        S *__restrict__ qout, C &lmax, C &min_rp, C &sum_l)
+{
+    constexpr int N = 5;
+    C qn[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxy[k] + (upper[k] - lower[k]));
+    const int64_t prow = (int64_t)(zz + 1) * EE + (y + 1) * E;
+    store_volume<N>(qout + (prow + x + 1) * N, qn);
+    Prim<3, C> st = primitives<3>(qn, g);
+    const C l = max_eigenvalue<3>(st);
+    min_rp = min_rp < qn[0] ? min_rp : qn[0];
+    min_rp = min_rp < st.p ? min_rp : st.p;
+    sum_l += l;
+    lmax = fv_max(lmax, l);
+    if (x == 0) {
+        C hv[N];
+        if (periodic) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) hv[k] = qn[k];
+            store_volume<N>(qout + (prow + P + 1) * N, hv);
+        } else {
+            load_volume<N>(qin + prow * N, hv);
+            store_volume<N>(qout + prow * N, hv);
+        }
+    }
+    if (x == P - 1) {
+        C hv[N];
+        if (periodic) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) hv[k] = qn[k];
+            store_volume<N>(qout + prow * N, hv);
+        } else {
+            load_volume<N>(qin + (prow + P + 1) * N, hv);
+            store_volume<N>(qout + (prow + P + 1) * N, hv);
+        }
+    }
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(kMaxThreads3, MinBlocks3<C>::value) k_sweep3d(Sweep3Params sp, int plane_bytes, int chunk)
+{
+    constexpr int N = 5;
+    extern __shared__ __align__(16) unsigned char smem3[];
+    const int P = sp.p, E = P + 2, EE = E * E;
+    // layout: ring[kRing3][EE*N] (S) | Fx[N][EE] | Lx[EE] | Fy[N][EE] | Ly[EE] | red[32]
+    unsigned char *ring = smem3;
+    const int ring_plane = (plane_bytes + 15) & ~15;
+    C *sFx = reinterpret_cast<C *>(ring + kRing3 * ring_plane);
+    C *sLx = sFx + N * EE;
+    C *sFy = sLx + EE;
+    C *sLy = sFy + N * EE;
+    C *red = sLy + EE;
+
+    const int patch = __ldg(sp.order + sp.first + blockIdx.x);
+    const int64_t base = __ldg(sp.b.elem_off + patch);
+    const S *__restrict__ qin = static_cast<const S *>(sp.q_in) + base;
+    S *__restrict__ qout = static_cast<S *>(sp.q_out) + base;
+    const unsigned char *gpatch = reinterpret_cast<const unsigned char *>(qin);
+    const bool periodic = sp.b.halo_mode == 1;
+    const Gas<C> g = gas3<C>(sp);
+
+    const int t = threadIdx.x;
+    const bool owner = t < P * P;
+    const int x = owner ? t % P : 0, y = owner ? t / P : 0;
+    const int cell = (y + 1) * E + (x + 1);                  // in-plane index
+    const double h = __ldg(sp.dx + patch);
+    const C sc = half_ratio3<C>(__ldg(sp.dt + patch), h);
+
+    // ring cells of a plane: thread t < 4P evaluates one halo volume
+    int hx = 0, hy = 0, hdir = 0, hsrc = 0, hcell = 0;
+    const bool ring_thread = t < 4 * P;
+    if (ring_thread) {
+        const int side = t / P, r = t - side * P;
+        if (side == 0) { hx = -1; hy = r; hdir = 0; }
+        else if (side == 1) { hx = P; hy = r; hdir = 0; }
+        else if (side == 2) { hx = r; hy = -1; hdir = 1; }
+        else { hx = r; hy = P; hdir = 1; }
+        hcell = (hy + 1) * E + (hx + 1);
+        const int sx = periodic ? wrap(hx, P) : hx, sy = periodic ? wrap(hy, P) : hy;
+        hsrc = (sy + 1) * E + (sx + 1);
+    }
+    auto src_plane = [&](int z) { return periodic ? wrap(z, P) : z; };
+    auto wrapped = [&](int xx, int yy) {
+        if (periodic) { xx = wrap(xx, P); yy = wrap(yy, P); }
+        return (yy + 1) * E + (xx + 1);
+    };
+    auto plane_ptr = [&](int z) {               // ring slot of plane z in [-1, P]
+        return reinterpret_cast<const S *>(ring + ((z + 1) % kRing3) * ring_plane);
+    };
+
+    // prologue: planes -1 .. kRing3-3
+    const unsigned ring_s = smem_addr(ring);
+#pragma unroll
+    for (int r = 0; r < kRing3 - 1; ++r) {
+        const int z = r - 1;
+        if (z <= P)
+            copy_plane(ring_s + ((z + 1) % kRing3) * ring_plane,
+                       gpatch + (int64_t)(src_plane(z) + 1) * plane_bytes, plane_bytes, chunk);
+        cp_commit();
+    }
+
+    // carried from plane z-1: its state, physical F_z and lambda_z, its x/y
+    // face difference and its lower z face
+    C qp[N], Fzp[N], lzp = C(0), dxy[N], Fzlow[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) { qp[k] = C(1); Fzp[k] = C(0); dxy[k] = C(0); Fzlow[k] = C(0); }
+    C lmax = C(0), min_rp = C(INFINITY), sum_l = C(0);
+
+    for (int z = -1; z <= P; ++z) {
+        cp_wait<kRing3 - 2>();
+        __syncthreads();                                     // plane z visible; plane z-1 reads done
+        {
+            const int zn = z + kRing3 - 1;
+            if (zn <= P)
+                copy_plane(ring_s + ((zn + 1) % kRing3) * ring_plane,
+                           gpatch + (int64_t)(src_plane(zn) + 1) * plane_bytes, plane_bytes, chunk);
+            cp_commit();
+        }
+        const S *pl = plane_ptr(z);
+        C q[N];
+        if (owner) {
+            load_volume<N>(pl + wrapped(x, y) * N, q);
+        } else {
+#pragma unroll
+            for (int k = 0; k < N; ++k) q[k] = C(1);
+            q[N - 1] = C(4);
+        }
+        if (z == -1) {                                       // lower halo plane
+            physics_dir<2>(q, g, Fzp, lzp);
+#pragma unroll
+            for (int k = 0; k < N; ++k) qp[k] = q[k];
+            continue;
+        }
+        if (z == P) {                                        // upper halo plane closes plane P-1
+            C Fz[N], lz, Fh[N];
+            physics_dir<2>(q, g, Fz, lz);
+            rusanov2<N>(qp, q, Fzp, Fz, lzp, lz, Fh);
+            if (owner)
+                finish3<S, C>(P - 1, Fh, qp, dxy, Fzlow, sc, g, x, y, P, E, EE, periodic, qin, qout, lmax,
+                              min_rp, sum_l);
+            continue;
+        }
+
+        // interior plane z: full physics of the own volume, published
+        Prim<3, C> s = primitives<3>(q, g);
+        C Fx[N], Fy[N], Fz[N];
+        flux<3>(q, s, 0, Fx);
+        flux<3>(q, s, 1, Fy);
+        flux<3>(q, s, 2, Fz);
+        const C lx = eigenvalue<3>(s, 0), ly = eigenvalue<3>(s, 1), lz = eigenvalue<3>(s, 2);
+        if (owner) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) { sFx[k * EE + cell] = Fx[k]; sFy[k * EE + cell] = Fy[k]; }
+            sLx[cell] = lx;
+            sLy[cell] = ly;
+        }
+        if (ring_thread) {
+            C hq[N], hF[N], hl;
+            load_volume<N>(pl + hsrc * N, hq);
+            if (hdir == 0) physics_dir<0>(hq, g, hF, hl);
+            else physics_dir<1>(hq, g, hF, hl);
+            C *dF = hdir == 0 ? sFx : sFy;
+            C *dL = hdir == 0 ? sLx : sLy;
+#pragma unroll
+            for (int k = 0; k < N; ++k) dF[k * EE + hcell] = hF[k];
+            dL[hcell] = hl;
+        }
+
+        // z face below plane z closes plane z-1; then plane z becomes the carry
+        {
+            C Fzl[N];
+            rusanov2<N>(qp, q, Fzp, Fz, lzp, lz, Fzl);
+            if (z > 0 && owner)
+                finish3<S, C>(z - 1, Fzl, qp, dxy, Fzlow, sc, g, x, y, P, E, EE, periodic, qin, qout, lmax,
+                              min_rp, sum_l);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                Fzlow[k] = Fzl[k];
+                Fzp[k] = Fz[k];
+                qp[k] = q[k];
+            }
+            lzp = lz;
+        }
+        __syncthreads();                                     // F and lambda of the plane published
+
+        // x and y faces of the own volume, from the published fluxes
+        C d[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) d[k] = C(0);
+        if (owner) {
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                const C *sF = n == 0 ? sFx : sFy;
+                const C *sL = n == 0 ? sLx : sLy;
+                const int dxn = n == 0 ? 1 : 0, dyn = n == 0 ? 0 : 1;
+                const int cl = (y - dyn + 1) * E + (x - dxn + 1), cr = (y + dyn + 1) * E + (x + dxn + 1);
+                C qL[N], qR[N], FL[N], FR[N], Fc[N], hl[N], hr[N];
+                load_volume<N>(pl + wrapped(x - dxn, y - dyn) * N, qL);
+                load_volume<N>(pl + wrapped(x + dxn, y + dyn) * N, qR);
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    FL[k] = sF[k * EE + cl];
+                    FR[k] = sF[k * EE + cr];
+                    Fc[k] = sF[k * EE + cell];
+                }
+                const C lc = sL[cell];
+                rusanov2<N>(qL, qp, FL, Fc, sL[cl], lc, hl);
+                rusanov2<N>(qp, qR, Fc, FR, lc, sL[cr], hr);
+#pragma unroll
+                for (int k = 0; k < N; ++k) d[k] += hr[k] - hl[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) dxy[k] = d[k];
+    }
+    cp_wait<0>();
+
+    // per-patch maximum eigenvalue, next time step, health flag
+    const bool bad = owner && (!(min_rp > C(0)) || !(sum_l < C(INFINITY)));
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(sp.b.flags, FV_FLAG_NONPHYSICAL);
+    if (sp.lambda_out || sp.dt_next_out) {
+        lmax = block_max_nonneg(lmax, red);
+        if (threadIdx.x == 0) {
+            const double l = double(lmax);
+            if (sp.lambda_out) sp.lambda_out[patch] = l;
+            if (sp.dt_next_out) sp.dt_next_out[patch] = cfl_dt(sp.cfl, h, 3, l);
+        }
+    }
+}
+
+size_t smem3_bytes(int P, int precision)
+{
+    const size_t E = P + 2, EE = E * E, N = 5;
+    const size_t s = precision == PREC_F64 ? 8 : (precision == PREC_F32 ? 4 : 2);
+    const size_t c = precision == PREC_F64 ? 8 : 4;
+    const size_t plane = (EE * N * s + 15) & ~size_t(15);
+    return kRing3 * plane + (2 * N + 2) * EE * c + 32 * c;
+}
+
+// Largest power of two <= 16 dividing `bytes`.
+int pow2_align(size_t bytes)
+{
+    int a = 16;
+    while (a > 1 && bytes % a != 0) a >>= 1;
+    return a;
+}
+
+template <typename S>
+cudaError_t launch3(const Sweep3Params &sp, int chunk, cudaStream_t st, int precision)
+{
+    using C = typename StorageTraits<S>::Compute;
+    const int P = sp.p;
+    const int plane_bytes = (P + 2) * (P + 2) * 5 * (int)sizeof(S);
+    const size_t smem = smem3_bytes(P, precision);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep3d<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int threads = std::max(32, ((P * P + 31) / 32) * 32);
+    k_sweep3d<S, C><<<sp.count, threads, smem, st>>>(sp, plane_bytes, std::min(chunk, pow2_align(plane_bytes)));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused3d_supported(const BatchView &b, int precision)
+{
+    if (b.dim != 3 || b.num_patches <= 0) return false;
+    // cp.async copies 4, 8 or 16 bytes: every patch and plane must start on
+    // a 4-byte boundary (bfloat16 patches of odd edge length do not)
+    if (b.align_bytes < 4) return false;
+    return b.max_p * b.max_p <= kMaxThreads3 && smem3_bytes(b.max_p, precision) <= 227 * 1024;
+}
+
+cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepArgs &a, const FusedPlan &plan,
+                                  cudaStream_t st)
+{
+    Sweep3Params sp;
+    sp.b = b;
+    sp.q_in = a.q_in;
+    sp.q_out = a.q_out;
+    sp.dx = a.dx;
+    sp.dt = a.dt;
+    sp.lambda_out = a.lambda_out;
+    sp.dt_next_out = a.dt_next_out;
+    sp.cfl = a.cfl;
+    sp.gamma_f = float(b.gamma);
+    sp.gm1_f = float(b.gamma - 1.0);
+    sp.order = plan.order;
+    // every patch base is a multiple of the smallest power-of-two alignment
+    // of all patch sizes in bytes (the buffer itself is 16-byte aligned)
+    const size_t es = precision == PREC_F64 ? 8 : (precision == PREC_F32 ? 4 : 2);
+    int chunk = 16;
+    for (int c = 0; c < plan.num_classes; ++c) {
+        const size_t E = plan.class_p[c] + 2;
+        chunk = std::min(chunk, pow2_align(E * E * E * 5 * es));
+    }
+    for (int c = 0; c < plan.num_classes; ++c) {
+        sp.first = plan.class_begin[c];
+        sp.count = plan.class_end[c] - plan.class_begin[c];
+        sp.p = plan.class_p[c];
+        cudaError_t e;
+        if (precision == PREC_F64) e = launch3<double>(sp, chunk, st, precision);
+        else if (precision == PREC_F32) e = launch3<float>(sp, chunk, st, precision);
+        else e = launch3<__nv_bfloat16>(sp, chunk, st, precision);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fv

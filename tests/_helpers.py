@@ -66,12 +66,32 @@ def patches_interior(flat, dim, patch_size):
     return out
 
 
-def batch_rel_linf(a, b, dim, patch_size):
-    """Relative L-infinity error over the interiors of a whole batch, each
-    unknown normalised by its largest magnitude in ``b``."""
-    ia = patches_interior(a, dim, patch_size)
-    ib = patches_interior(b, dim, patch_size)
+def state_rel_linf(a, b):
+    """Relative L-infinity error of a state: the largest |a - b| over volumes
+    and unknowns divided by the largest |b| over volumes and unknowns."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0))
+
+
+def _interiors(a, b, dim, patch_size):
     N = dim + 2
-    A = np.concatenate([x.reshape(-1, N) for x in ia])
-    B = np.concatenate([x.reshape(-1, N) for x in ib])
-    return rel_linf(A, B, dim)
+    A = np.concatenate([x.reshape(-1, N) for x in patches_interior(a, dim, patch_size)])
+    B = np.concatenate([x.reshape(-1, N) for x in patches_interior(b, dim, patch_size)])
+    return A, B
+
+
+def batch_rel_linf(a, b, dim, patch_size):
+    """Relative L-infinity error over the interiors of a whole batch
+    (normalised by the oracle state's largest magnitude, all unknowns)."""
+    A, B = _interiors(a, b, dim, patch_size)
+    return state_rel_linf(A, B)
+
+
+def batch_rel_linf_components(a, b, dim, patch_size):
+    """Per-unknown relative L-infinity errors (each unknown normalised by its
+    own largest magnitude), for reporting."""
+    A, B = _interiors(a, b, dim, patch_size)
+    return [float(np.max(np.abs(A[:, k] - B[:, k])) / max(np.max(np.abs(B[:, k])), 1e-300))
+            for k in range(dim + 2)]

@@ -18,3 +18,18 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(autouse=True)
+def _sync_after_gpu_test(request):
+    """Synchronise after every GPU test so an asynchronous device error is
+    reported by the test that caused it."""
+    yield
+    if request.node.get_closest_marker("gpu") is None:
+        return
+    try:
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+    except RuntimeError as e:
+        pytest.fail("device error after %s: %s" % (request.node.nodeid, e))

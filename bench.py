@@ -48,8 +48,11 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the secondary 3D / uneven workload lines")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--profile", choices=["fused_f32", "fused_f64", "cascade_f64", "tile_f32"],
+    ap.add_argument("--profile", choices=["fused_f32", "fused_f64", "cascade_f64", "tile_f32",
+                                          "fused3d_f32", "fused3d16_f32"],
                     default=None, help="no timing: run a few launches of one form for ncu")
     ap.add_argument("--patches", type=int, default=None,
                     help="with --profile: batch size (default 65536, state larger than L2)")
@@ -366,6 +369,10 @@ def run_ours(args):
            "d2h_bytes_per_step": int(state_bytes + T * 8),
            "wall_s": time.perf_counter() - t_e2e}
 
+    if not args.no_other_workloads and world == 1:
+        forms_other = other_workloads(dev, stream, flush_l2, args.steps)
+    else:
+        forms_other = None
     clk = clocks.stop()
 
     if rank != 0:
@@ -403,6 +410,8 @@ def run_ours(args):
                       "parallelism": "replicas (patches independent; no collective)"},
            "roofline": roofline, "gpu_launches": launches, "e2e": e2e, "clocks": clk,
            "forms": forms}
+    if forms_other is not None:
+        out["workloads"] = forms_other
     if "cascade_f64" in forms:
         out["speedup_fused_f32_vs_cascade_f64"] = forms["fused_f32"]["value"] / forms["cascade_f64"]["value"]
 
@@ -420,6 +429,126 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return out
+
+
+def other_workloads(dev, stream, flush_l2, steps):
+    """Secondary lines: the 3D periodic pulse (FP32 and BF16 storage), the
+    uneven 2D batch (200 steps in one CUDA graph) and the 3D 16^3 batch
+    (fused FP32 vs plain FP64 cascade).  Single steps are timed with L2
+    flushed like the headline; graph runs are L2-warm by nature."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb, inputs
+    peak = _peak_hbm()
+    res = {}
+
+    def setup(w, precision, form=None):
+        b = fb.FVBatch(w.dim, w.patch_size, precision=precision, halo_mode=w.halo_mode,
+                       form=form, stream=stream.cuda_stream)
+        dtype = {0: torch.float64, 1: torch.float32, 2: torch.bfloat16}[precision]
+        qa = torch.from_numpy(w.Q0).to(device=dev).to(dtype)
+        qb = qa.clone()
+        dx = torch.tensor(w.dx, device=dev)
+        lam = torch.zeros(w.num_patches, dtype=torch.float64, device=dev)
+        dts = [torch.zeros_like(lam), torch.zeros_like(lam)]
+        b.max_eigenvalue(qa, lam)
+        b.cfl_time_step(lam, dx, w.cfl, dts[0])
+        return b, [qa, qb], dx, lam, dts
+
+    def single_steps(b, qs, dx, lam, dts, k, cfl):
+        for s in range(3):
+            b.update(qs[s & 1], qs[1 - (s & 1)], dx, dts[s & 1], lam, dts[1 - (s & 1)], cfl)
+        tot = 0.0
+        for s in range(k):
+            i = (3 + s) & 1
+            flush_l2()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.update(qs[i], qs[1 - i], dx, dts[i], lam, dts[1 - i], cfl)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        b.status()
+        return tot / k
+
+    def bytes_per_volume(w, es):
+        p = w.patch_size.astype(np.float64)
+        N = w.dim + 2
+        reads = p ** w.dim + (0 if w.halo_mode == 1 else 2 * w.dim * p ** (w.dim - 1))
+        return float(np.sum(N * es * (reads + p ** w.dim)) / np.sum(p ** w.dim))
+
+    k = max(5, min(30, steps // 4))
+    # 3D periodic pulse, 4096 patches of 8^3
+    w3 = inputs.config(3, dtype=np.float32)
+    for name, prec, es in (("3d_p8_T4096_periodic_f32", 1, 4), ("3d_p8_T4096_periodic_bf16", 2, 2)):
+        b, qs, dx, lam, dts = setup(w3, prec)
+        scratch = qs[0].clone()
+        b.tune(qs[0], scratch, dx, dts[0])
+        del scratch
+        ms = single_steps(b, qs, dx, lam, dts, k, w3.cfl)
+        bpv = bytes_per_volume(w3, es)
+        res[name] = {"value": w3.interior_volumes / (ms / 1e3), "ms_per_step": ms,
+                     "bytes_per_volume": bpv, "achieved_gbs": w3.interior_volumes * bpv / (ms / 1e3) / 1e9,
+                     "roofline_frac": w3.interior_volumes * bpv / (ms / 1e3) / 1e9 / peak,
+                     "kernel": b.describe()}
+        b.close()
+    # uneven 2D batch, 50,000 patches, 200 steps in one graph
+    w4 = inputs.config(4, dtype=np.float32)
+    b, qs, dx, lam, dts = setup(w4, 1)
+    scratch = qs[0].clone()
+    b.tune(qs[0], scratch, dx, dts[0])
+    del scratch
+    ms1 = single_steps(b, qs, dx, lam, dts, k, w4.cfl)
+    b.run(qs[0], qs[1], dx, dts[0], dts[1], lam, w4.steps, w4.cfl, True)    # capture
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(qs[0], qs[1], dx, dts[0], dts[1], lam, w4.steps, w4.cfl, True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.status()
+    gms = e0.elapsed_time(e1)
+    bpv = bytes_per_volume(w4, 4)
+    res["2d_uneven_T50000_f32"] = {
+        "value_graph_%dsteps" % w4.steps: w4.interior_volumes * w4.steps / (gms / 1e3),
+        "ms_per_step_graph": gms / w4.steps, "value_single_step": w4.interior_volumes / (ms1 / 1e3),
+        "ms_per_step_single": ms1, "bytes_per_volume": bpv,
+        "roofline_frac_single_step": w4.interior_volumes * bpv / (ms1 / 1e3) / 1e9 / peak,
+        "launches_per_step": b.launches_per_update(), "kernel": b.describe()}
+    b.close()
+    del qs
+    # 3D 16^3, 32,768 patches (3.8 GB FP32 state)
+    w5 = inputs.config(5, dtype=np.float32)
+    b, qs, dx, lam, dts = setup(w5, 1)
+    ms = single_steps(b, qs, dx, lam, dts, max(3, k // 3), w5.cfl)
+    bpv = bytes_per_volume(w5, 4)
+    res["3d_p16_T32768_f32"] = {"value": w5.interior_volumes / (ms / 1e3), "ms_per_step": ms,
+                                "bytes_per_volume": bpv,
+                                "achieved_gbs": w5.interior_volumes * bpv / (ms / 1e3) / 1e9,
+                                "roofline_frac": w5.interior_volumes * bpv / (ms / 1e3) / 1e9 / peak,
+                                "kernel": b.describe()}
+    b.close()
+    del qs
+    torch.cuda.empty_cache()
+    try:
+        b, qs, dx, lam, dts = setup(w5, 0, fb.FV_FORM_CASCADE)
+        ms = single_steps(b, qs, dx, lam, dts, 2, w5.cfl)
+        res["3d_p16_T32768_cascade_f64"] = {"value": w5.interior_volumes / (ms / 1e3), "ms_per_step": ms,
+                                            "scratch_bytes": b.scratch_bytes()}
+        res["3d_p16_T32768_speedup_fused_f32_vs_cascade_f64"] = (
+            res["3d_p16_T32768_f32"]["value"] / res["3d_p16_T32768_cascade_f64"]["value"])
+        b.close()
+        del qs
+    except Exception as e:            # e.g. not enough device memory for the cascade scratch
+        res["3d_p16_T32768_cascade_f64"] = {"unavailable": str(e)[:200]}
+    torch.cuda.empty_cache()
+    return res
+
+
+def _peak_hbm():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
 
 
 def _smi_id(torch, dev):
@@ -487,12 +616,18 @@ def run_profile(args):
     import torch
     from paper_2306_16731_gb300 import build, fvbatch as fb, inputs
     build.build()
-    T = args.patches or 65536
-    w = inputs.uniform_batch(2, [16] * T, seed=2, dx=0.01, dtype=np.float32)
     form_name, prec_name = args.profile.split("_")
+    if form_name.startswith("fused3d"):
+        p3 = 16 if form_name == "fused3d16" else 8
+        T = args.patches or (4096 if p3 == 16 else 16384)
+        w = inputs.uniform_batch(3, [p3] * T, seed=3, dx=0.01, dtype=np.float32)
+        form_name = "fused"
+    else:
+        T = args.patches or 65536
+        w = inputs.uniform_batch(2, [16] * T, seed=2, dx=0.01, dtype=np.float32)
     prec = {"f32": fb.FV_F32, "f64": fb.FV_F64}[prec_name]
     form = {"fused": fb.FV_FORM_FUSED, "cascade": fb.FV_FORM_CASCADE, "tile": fb.FV_FORM_TILE}[form_name]
-    b = fb.FVBatch(2, w.patch_size, precision=prec, form=form)
+    b = fb.FVBatch(w.dim, w.patch_size, precision=prec, form=form)
     dtype = torch.float32 if prec == fb.FV_F32 else torch.float64
     qa = torch.from_numpy(w.Q0).to("cuda", dtype)
     qb = qa.clone()

@@ -109,9 +109,7 @@ __device__ __forceinline__ void physics_dir(const C (&q)[5], Gas<C> g, C (&F)[5]
 
 // Finish the owner's volume of plane zz (stored at memory plane zz+1):
 // Q_new = Q - dt/(2h) ((x/y difference) + (upper - lower z face)), store,
-// fold its eigenvalue into the running maximum and health, and write the
-// row's x-halo volume (fixed: Q_in's value; periodic: the wrapped new
-// value, since the volume at x = 0 is the halo at x = P and vice versa).
+// fold its eigenvalue into the running maximum and health.
 template <typename S, typename C>
 __device__ __forceinline__ void finish3(int zz, const C (&upper)[5], const C (&qp)[5], const C (&dxy)[5],
                                         const C (&lower)[5], C sc, Gas<C> g, int x, int y, int P, int E,
@@ -130,27 +128,29 @@ __device__ __forceinline__ void finish3(int zz, const C (&upper)[5], const C (&q
     min_rp = min_rp < st.p ? min_rp : st.p;
     sum_l += l;
     lmax = fv_max(lmax, l);
+    // periodic patches: the volume at x = 0 is the halo volume at x = P and
+    // vice versa; writing it keeps rows whole (fixed halos are copied from
+    // the staged plane by fixed_halo3 instead)
+    if (periodic && x == 0) store_volume<N>(qout + (prow + P + 1) * N, qn);
+    if (periodic && x == P - 1) store_volume<N>(qout + prow * N, qn);
+}
+
+// Fixed halos: copy the x-halo volumes of row y of plane z from the staged
+// plane to Q_out while the plane is current, so that with the interior
+// written one plane later every 32-byte sector of the row is written whole.
+template <typename S>
+__device__ __forceinline__ void fixed_halo3(const S *pl, S *__restrict__ qout, int z, int x, int y, int P, int E,
+                                            int EE)
+{
+    constexpr int N = 5;
+    const int64_t prow = (int64_t)(z + 1) * EE + (y + 1) * E;
     if (x == 0) {
-        C hv[N];
-        if (periodic) {
 #pragma unroll
-            for (int k = 0; k < N; ++k) hv[k] = qn[k];
-            store_volume<N>(qout + (prow + P + 1) * N, hv);
-        } else {
-            load_volume<N>(qin + prow * N, hv);
-            store_volume<N>(qout + prow * N, hv);
-        }
+        for (int k = 0; k < N; ++k) qout[prow * N + k] = pl[((y + 1) * E) * N + k];
     }
     if (x == P - 1) {
-        C hv[N];
-        if (periodic) {
 #pragma unroll
-            for (int k = 0; k < N; ++k) hv[k] = qn[k];
-            store_volume<N>(qout + prow * N, hv);
-        } else {
-            load_volume<N>(qin + (prow + P + 1) * N, hv);
-            store_volume<N>(qout + (prow + P + 1) * N, hv);
-        }
+        for (int k = 0; k < N; ++k) qout[(prow + P + 1) * N + k] = pl[((y + 1) * E + P + 1) * N + k];
     }
 }
 
@@ -258,6 +258,8 @@ __global__ void __launch_bounds__(kMaxThreads3, MinBlocks3<C>::value) k_sweep3d(
                               min_rp, sum_l);
             continue;
         }
+
+        if (owner && !periodic) fixed_halo3<S>(pl, qout, z, x, y, P, E, EE);
 
         // interior plane z: full physics of the own volume, published
         Prim<3, C> s = primitives<3>(q, g);
@@ -381,6 +383,313 @@ cudaError_t launch3(const Sweep3Params &sp, int chunk, cudaStream_t st, int prec
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Edge lengths that are multiples of 8: one warp per 8 x 8 column block of a
+// patch (the patch's (p/8)^2 warps share only the plane ring), two columns
+// per lane: lane = (x, yb) with x = lane % 8, yb = lane / 8, owning rows yb
+// (cell A) and yb + 4 (cell B) of the block.
+//   * x faces: the right neighbour's Q, F_x, lambda_x by shuffle (lane + 1),
+//     the left face as the left lane's right face (lane - 1);
+//   * y faces: the upper neighbour by shuffle (lane + 8), cell A of the top
+//     lane row taking the own cell B; lower faces by shuffle back;
+//   * the 32 faces between the block and its ring (patch halo or the
+//     neighbouring block's volumes) are computed first, one per lane, into
+//     shared memory, so no lane does extra face work inside the sweep;
+//   * z faces by the register recurrence, as in the general kernel.
+constexpr int kRingB = 3;
+
+template <int N, typename C>
+__device__ __forceinline__ void shfl_vec(C (&o)[N], const C (&v)[N], int delta, bool down)
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        o[k] = down ? __shfl_down_sync(0xffffffffu, v[k], delta) : __shfl_up_sync(0xffffffffu, v[k], delta);
+}
+
+// Flux and eigenvalue along x (ydir false) or y (ydir true) without a
+// branch: the normal velocity and the pressure slot are selected.
+template <typename C>
+__device__ __forceinline__ void physics_sel(const C (&q)[5], Gas<C> g, bool ydir, C (&F)[5], C &lam)
+{
+    Prim<3, C> s = primitives<3>(q, g);
+    const C un = ydir ? s.u[1] : s.u[0];
+    F[0] = ydir ? q[2] : q[1];
+    F[1] = q[1] * un + (ydir ? C(0) : s.p);
+    F[2] = q[2] * un + (ydir ? s.p : C(0));
+    F[3] = q[3] * un;
+    F[4] = (q[4] + s.p) * un;
+    lam = fv_abs(un) + s.c;
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plane_bytes, int chunk)
+{
+    constexpr int N = 5;
+    extern __shared__ __align__(16) unsigned char smemb[];
+    const int P = sp.p, E = P + 2, EE = E * E, nb = P / 8;
+    const int ring_plane = (plane_bytes + 15) & ~15;
+    unsigned char *ring = smemb;
+    C *bfall = reinterpret_cast<C *>(ring + kRingB * ring_plane);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C *bf = bfall + warp * 32 * N;                   // this warp's 32 boundary faces
+    C *red = bfall + (blockDim.x >> 5) * 32 * N;     // 32 slots
+
+    const int patch = __ldg(sp.order + sp.first + blockIdx.x);
+    const int64_t base = __ldg(sp.b.elem_off + patch);
+    const S *__restrict__ qin = static_cast<const S *>(sp.q_in) + base;
+    S *__restrict__ qout = static_cast<S *>(sp.q_out) + base;
+    const unsigned char *gpatch = reinterpret_cast<const unsigned char *>(qin);
+    const bool periodic = sp.b.halo_mode == 1;
+    const Gas<C> g = gas3<C>(sp);
+    const double h = __ldg(sp.dx + patch);
+    const C sc = half_ratio3<C>(__ldg(sp.dt + patch), h);
+
+    const int x0 = (warp % nb) * 8, y0 = (warp / nb) * 8;
+    const int x = lane & 7, yb = lane >> 3;
+    const int gx = x0 + x, gyA = y0 + yb, gyB = y0 + yb + 4;
+    const int cellA = (gyA + 1) * E + (gx + 1), cellB = (gyB + 1) * E + (gx + 1);
+
+    // this lane's ring volume and the interior volume next to it
+    const int side = lane >> 3, r = lane & 7;
+    int rx, ry, ix, iy;
+    if (side == 0) { rx = x0 - 1; ry = y0 + r; ix = x0; iy = ry; }
+    else if (side == 1) { rx = x0 + 8; ry = y0 + r; ix = x0 + 7; iy = ry; }
+    else if (side == 2) { rx = x0 + r; ry = y0 - 1; ix = rx; iy = y0; }
+    else { rx = x0 + r; ry = y0 + 8; ix = rx; iy = y0 + 7; }
+    if (periodic) { rx = wrap(rx, P); ry = wrap(ry, P); }
+    const int rcell = (ry + 1) * E + (rx + 1), icell = (iy + 1) * E + (ix + 1);
+
+    const unsigned ring_s = smem_addr(ring);
+    auto src_plane = [&](int z) { return periodic ? wrap(z, P) : z; };
+#pragma unroll
+    for (int rr = 0; rr < kRingB - 1; ++rr) {
+        const int z = rr - 1;
+        if (z <= P)
+            copy_plane(ring_s + ((z + 1) % kRingB) * ring_plane,
+                       gpatch + (int64_t)(src_plane(z) + 1) * plane_bytes, plane_bytes, chunk);
+        cp_commit();
+    }
+
+    C qpA[N], FzpA[N], lzpA = C(0), dA[N], FlowA[N];
+    C qpB[N], FzpB[N], lzpB = C(0), dB[N], FlowB[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        qpA[k] = qpB[k] = C(0);
+        FzpA[k] = FzpB[k] = C(0);
+        dA[k] = dB[k] = C(0);
+        FlowA[k] = FlowB[k] = C(0);
+    }
+    C lmax = C(0), min_rp = C(INFINITY), sum_l = C(0);
+
+    for (int z = -1; z <= P; ++z) {
+        cp_wait<kRingB - 2>();
+        __syncthreads();
+        {
+            const int zn = z + kRingB - 1;
+            if (zn <= P)
+                copy_plane(ring_s + ((zn + 1) % kRingB) * ring_plane,
+                           gpatch + (int64_t)(src_plane(zn) + 1) * plane_bytes, plane_bytes, chunk);
+            cp_commit();
+        }
+        const S *pl = reinterpret_cast<const S *>(ring + ((z + 1) % kRingB) * ring_plane);
+
+        if (z == -1 || z == P) {
+            C qA[N], qB[N], FzA[N], FzB[N], lzA, lzB;
+            load_volume<N>(pl + cellA * N, qA);
+            load_volume<N>(pl + cellB * N, qB);
+            physics_dir<2>(qA, g, FzA, lzA);
+            physics_dir<2>(qB, g, FzB, lzB);
+            if (z == P) {
+                C FhA[N], FhB[N];
+                rusanov2<N>(qpA, qA, FzpA, FzA, lzpA, lzA, FhA);
+                rusanov2<N>(qpB, qB, FzpB, FzB, lzpB, lzB, FhB);
+                finish3<S, C>(P - 1, FhA, qpA, dA, FlowA, sc, g, gx, gyA, P, E, EE, periodic, qin, qout, lmax,
+                              min_rp, sum_l);
+                finish3<S, C>(P - 1, FhB, qpB, dB, FlowB, sc, g, gx, gyB, P, E, EE, periodic, qin, qout, lmax,
+                              min_rp, sum_l);
+            } else {
+#pragma unroll
+                for (int k = 0; k < N; ++k) { qpA[k] = qA[k]; qpB[k] = qB[k]; FzpA[k] = FzA[k]; FzpB[k] = FzB[k]; }
+                lzpA = lzA;
+                lzpB = lzB;
+            }
+            continue;
+        }
+
+        if (!periodic) {
+            fixed_halo3<S>(pl, qout, z, gx, gyA, P, E, EE);
+            fixed_halo3<S>(pl, qout, z, gx, gyB, P, E, EE);
+        }
+
+        // boundary faces of the block, one per lane (x faces for sides 0, 1,
+        // y faces for sides 2, 3; the ring volume is the lower one for sides
+        // 0 and 2)
+        {
+            C qr[N], qi[N], Fr[N], Fi[N], lr, li, Fh[N];
+            load_volume<N>(pl + rcell * N, qr);
+            load_volume<N>(pl + icell * N, qi);
+            const bool ydir = side >= 2, ring_low = (side & 1) == 0;
+            physics_sel(qr, g, ydir, Fr, lr);
+            physics_sel(qi, g, ydir, Fi, li);
+            C qL[N], qR[N], FL[N], FR[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                qL[k] = ring_low ? qr[k] : qi[k];
+                qR[k] = ring_low ? qi[k] : qr[k];
+                FL[k] = ring_low ? Fr[k] : Fi[k];
+                FR[k] = ring_low ? Fi[k] : Fr[k];
+            }
+            rusanov2<N>(qL, qR, FL, FR, ring_low ? lr : li, ring_low ? li : lr, Fh);
+#pragma unroll
+            for (int k = 0; k < N; ++k) bf[lane * N + k] = Fh[k];
+        }
+
+        // own volumes: physics, z faces, finish plane z-1
+        C qA[N], qB[N];
+        load_volume<N>(pl + cellA * N, qA);
+        load_volume<N>(pl + cellB * N, qB);
+        Prim<3, C> sA = primitives<3>(qA, g), sB = primitives<3>(qB, g);
+        {
+            C FzA[N], FzB[N], FlA[N], FlB[N];
+            flux<3>(qA, sA, 2, FzA);
+            flux<3>(qB, sB, 2, FzB);
+            const C lzA = eigenvalue<3>(sA, 2), lzB = eigenvalue<3>(sB, 2);
+            rusanov2<N>(qpA, qA, FzpA, FzA, lzpA, lzA, FlA);
+            rusanov2<N>(qpB, qB, FzpB, FzB, lzpB, lzB, FlB);
+            if (z > 0) {
+                finish3<S, C>(z - 1, FlA, qpA, dA, FlowA, sc, g, gx, gyA, P, E, EE, periodic, qin, qout, lmax,
+                              min_rp, sum_l);
+                finish3<S, C>(z - 1, FlB, qpB, dB, FlowB, sc, g, gx, gyB, P, E, EE, periodic, qin, qout, lmax,
+                              min_rp, sum_l);
+            }
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                FlowA[k] = FlA[k]; FlowB[k] = FlB[k];
+                FzpA[k] = FzA[k]; FzpB[k] = FzB[k];
+                qpA[k] = qA[k]; qpB[k] = qB[k];
+            }
+            lzpA = lzA;
+            lzpB = lzB;
+        }
+        __syncwarp();                                        // boundary faces visible
+
+        // x faces
+        {
+            C FxA[N], FxB[N], nq[N], nF[N], FrA[N], FrB[N], FlA[N], FlB[N];
+            flux<3>(qA, sA, 0, FxA);
+            flux<3>(qB, sB, 0, FxB);
+            const C lxA = eigenvalue<3>(sA, 0), lxB = eigenvalue<3>(sB, 0);
+            shfl_vec<N>(nq, qA, 1, true);
+            shfl_vec<N>(nF, FxA, 1, true);
+            C nl = __shfl_down_sync(0xffffffffu, lxA, 1);
+            rusanov2<N>(qA, nq, FxA, nF, lxA, nl, FrA);
+            shfl_vec<N>(nq, qB, 1, true);
+            shfl_vec<N>(nF, FxB, 1, true);
+            nl = __shfl_down_sync(0xffffffffu, lxB, 1);
+            rusanov2<N>(qB, nq, FxB, nF, lxB, nl, FrB);
+            if (x == 7) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) { FrA[k] = bf[(8 + yb) * N + k]; FrB[k] = bf[(12 + yb) * N + k]; }
+            }
+            shfl_vec<N>(FlA, FrA, 1, false);
+            shfl_vec<N>(FlB, FrB, 1, false);
+            if (x == 0) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) { FlA[k] = bf[yb * N + k]; FlB[k] = bf[(4 + yb) * N + k]; }
+            }
+#pragma unroll
+            for (int k = 0; k < N; ++k) { dA[k] = FrA[k] - FlA[k]; dB[k] = FrB[k] - FlB[k]; }
+        }
+        // y faces
+        {
+            C FyA[N], FyB[N], nq[N], nF[N], FuA[N], FuB[N], FdA[N], FdB[N], t[N];
+            flux<3>(qA, sA, 1, FyA);
+            flux<3>(qB, sB, 1, FyB);
+            const C lyA = eigenvalue<3>(sA, 1), lyB = eigenvalue<3>(sB, 1);
+            const bool top = yb == 3, bottom = yb == 0;
+            // upper face of A: neighbour lane + 8 (A); for the top lane row
+            // (row 3) it is row 4, the B of lane - 24
+            shfl_vec<N>(nq, qA, 8, true);
+            shfl_vec<N>(nF, FyA, 8, true);
+            C nl = __shfl_down_sync(0xffffffffu, lyA, 8);
+            {
+                C bq[N], bF[N];
+                shfl_vec<N>(bq, qB, 24, false);
+                shfl_vec<N>(bF, FyB, 24, false);
+                const C bl = __shfl_up_sync(0xffffffffu, lyB, 24);
+                if (top) {
+#pragma unroll
+                    for (int k = 0; k < N; ++k) { nq[k] = bq[k]; nF[k] = bF[k]; }
+                    nl = bl;
+                }
+            }
+            rusanov2<N>(qA, nq, FyA, nF, lyA, nl, FuA);
+            // upper face of B: neighbour lane + 8 (B), or the block's upper boundary
+            shfl_vec<N>(nq, qB, 8, true);
+            shfl_vec<N>(nF, FyB, 8, true);
+            nl = __shfl_down_sync(0xffffffffu, lyB, 8);
+            rusanov2<N>(qB, nq, FyB, nF, lyB, nl, FuB);
+            if (top) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) FuB[k] = bf[(24 + x) * N + k];
+            }
+            // lower faces: the lower lane's upper faces; row 4 (B of the bottom
+            // lane row) takes the upper face of row 3 (A of lane + 24)
+            shfl_vec<N>(FdA, FuA, 8, false);
+            shfl_vec<N>(FdB, FuB, 8, false);
+            shfl_vec<N>(t, FuA, 24, true);
+            if (bottom) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) { FdA[k] = bf[(16 + x) * N + k]; FdB[k] = t[k]; }
+            }
+#pragma unroll
+            for (int k = 0; k < N; ++k) { dA[k] += FuA[k] - FdA[k]; dB[k] += FuB[k] - FdB[k]; }
+        }
+        __syncwarp();                                        // boundary faces consumed
+    }
+    cp_wait<0>();
+
+    const bool bad = !(min_rp > C(0)) || !(sum_l < C(INFINITY));
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(sp.b.flags, FV_FLAG_NONPHYSICAL);
+    if (sp.lambda_out || sp.dt_next_out) {
+        lmax = block_max_nonneg(lmax, red);
+        if (threadIdx.x == 0) {
+            const double l = double(lmax);
+            if (sp.lambda_out) sp.lambda_out[patch] = l;
+            if (sp.dt_next_out) sp.dt_next_out[patch] = cfl_dt(sp.cfl, h, 3, l);
+        }
+    }
+}
+
+size_t smem3b_bytes(int P, int precision)
+{
+    const size_t E = P + 2, EE = E * E, N = 5;
+    const size_t s = precision == PREC_F64 ? 8 : (precision == PREC_F32 ? 4 : 2);
+    const size_t c = precision == PREC_F64 ? 8 : 4;
+    const size_t plane = (EE * N * s + 15) & ~size_t(15);
+    const size_t warps = (size_t)(P / 8) * (P / 8);
+    return kRingB * plane + warps * 32 * N * c + 32 * c;
+}
+
+template <typename S>
+cudaError_t launch3b(const Sweep3Params &sp, int chunk, cudaStream_t st, int precision)
+{
+    using C = typename StorageTraits<S>::Compute;
+    const int P = sp.p;
+    const int plane_bytes = (P + 2) * (P + 2) * 5 * (int)sizeof(S);
+    const size_t smem = smem3b_bytes(P, precision);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep3d_b8<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int threads = 32 * (P / 8) * (P / 8);
+    k_sweep3d_b8<S, C><<<sp.count, threads, smem, st>>>(sp, plane_bytes, std::min(chunk, pow2_align(plane_bytes)));
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 bool fused3d_supported(const BatchView &b, int precision)
@@ -389,7 +698,9 @@ bool fused3d_supported(const BatchView &b, int precision)
     // cp.async copies 4, 8 or 16 bytes: every patch and plane must start on
     // a 4-byte boundary (bfloat16 patches of odd edge length do not)
     if (b.align_bytes < 4) return false;
-    return b.max_p * b.max_p <= kMaxThreads3 && smem3_bytes(b.max_p, precision) <= 227 * 1024;
+    const bool general = b.max_p * b.max_p <= kMaxThreads3 && smem3_bytes(b.max_p, precision) <= 227 * 1024;
+    const bool blocks8 = precision != PREC_F64 && b.uniform_p > 0 && b.uniform_p % 8 == 0 && b.uniform_p <= 32;
+    return general || blocks8;
 }
 
 cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepArgs &a, const FusedPlan &plan,
@@ -420,7 +731,15 @@ cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepA
         sp.count = plan.class_end[c] - plan.class_begin[c];
         sp.p = plan.class_p[c];
         cudaError_t e;
-        if (precision == PREC_F64) e = launch3<double>(sp, chunk, st, precision);
+        // the block kernel needs 124 registers in float; double stays on the
+        // general kernel (it would spill)
+        const bool blocks8 = precision != PREC_F64 && sp.p % 8 == 0 && sp.p <= 32 &&
+                             smem3b_bytes(sp.p, precision) <= 227 * 1024;
+        if (blocks8) {
+            if (precision == PREC_F64) e = launch3b<double>(sp, chunk, st, precision);
+            else if (precision == PREC_F32) e = launch3b<float>(sp, chunk, st, precision);
+            else e = launch3b<__nv_bfloat16>(sp, chunk, st, precision);
+        } else if (precision == PREC_F64) e = launch3<double>(sp, chunk, st, precision);
         else if (precision == PREC_F32) e = launch3<float>(sp, chunk, st, precision);
         else e = launch3<__nv_bfloat16>(sp, chunk, st, precision);
         if (e != cudaSuccess) return e;

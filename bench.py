@@ -284,12 +284,10 @@ def run_ours(args):
     desc32 = b32.describe()
     launches = b32.launches_per_update() * args.steps
 
-    # max over ranks
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * vols * args.steps / (ms_max / 1e3)
+    # slowest rank decides; every rank advanced its own replica batch
+    from paper_2306_16731_gb300.multigpu import max_over_ranks, whole_job_rate
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = whole_job_rate(vols * args.steps, ms_max / 1e3, dist, dev)
 
     # the FP64 forms beside it (fewer steps: FP64 is slow on this part)
     forms = {}

@@ -169,8 +169,9 @@ __global__ void __launch_bounds__(kMaxThreads3, MinBlocks3<C>::value) k_sweep3d(
     C *sLy = sFy + N * EE;
     C *red = sLy + EE;
 
-    const int patch = __ldg(sp.order + sp.first + blockIdx.x);
-    const int64_t base = __ldg(sp.b.elem_off + patch);
+    const int patch = sp.b.uniform_p > 0 ? sp.first + (int)blockIdx.x : __ldg(sp.order + sp.first + blockIdx.x);
+    const int64_t base = sp.b.uniform_p > 0 ? (int64_t)patch * patch_cells(3, sp.b.uniform_p) * 5
+                                            : __ldg(sp.b.elem_off + patch);
     const S *__restrict__ qin = static_cast<const S *>(sp.q_in) + base;
     S *__restrict__ qout = static_cast<S *>(sp.q_out) + base;
     const unsigned char *gpatch = reinterpret_cast<const unsigned char *>(qin);
@@ -435,8 +436,9 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
     C *bf = bfall + warp * 32 * N;                   // this warp's 32 boundary faces
     C *red = bfall + (blockDim.x >> 5) * 32 * N;     // 32 slots
 
-    const int patch = __ldg(sp.order + sp.first + blockIdx.x);
-    const int64_t base = __ldg(sp.b.elem_off + patch);
+    const int patch = sp.b.uniform_p > 0 ? sp.first + (int)blockIdx.x : __ldg(sp.order + sp.first + blockIdx.x);
+    const int64_t base = sp.b.uniform_p > 0 ? (int64_t)patch * patch_cells(3, sp.b.uniform_p) * 5
+                                            : __ldg(sp.b.elem_off + patch);
     const S *__restrict__ qin = static_cast<const S *>(sp.q_in) + base;
     S *__restrict__ qout = static_cast<S *>(sp.q_out) + base;
     const unsigned char *gpatch = reinterpret_cast<const unsigned char *>(qin);

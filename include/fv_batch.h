@@ -112,8 +112,11 @@ int fv_batch_set_form(fv_batch_t *b, int form);
 /* Launch shape of the fused form: warps_per_block in [1, 16]; blocks_per_sm
  * 0 = one warp per work item (grid covers the work list), > 0 = that many
  * persistent blocks per SM taking items from a device counter, -1 =
- * persistent with as many blocks per SM as can be resident.  Results do not
- * depend on the shape (every shape computes the same arithmetic). */
+ * persistent with as many blocks per SM as can be resident, -2 = resident
+ * persistent warps taking items round-robin with the row stream running
+ * across items (2D batches of one edge length 8, 16 or 32; otherwise as -1).
+ * Results do not depend on the shape (every shape computes the same
+ * arithmetic). */
 int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per_sm);
 
 /* Rebind the batch to another stream (e.g. a capture stream). */

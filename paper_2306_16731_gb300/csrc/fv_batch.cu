@@ -370,7 +370,7 @@ int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     if (warps_per_block < 1 || warps_per_block > 16) return fail(FV_EINVAL, "warps_per_block must be in [1, 16]");
-    if (blocks_per_sm < -1 || blocks_per_sm > 32) return fail(FV_EINVAL, "blocks_per_sm must be in [-1, 32]");
+    if (blocks_per_sm < -2 || blocks_per_sm > 32) return fail(FV_EINVAL, "blocks_per_sm must be in [-2, 32]");
     b->plan.shape = fv::FusedShape{warps_per_block, blocks_per_sm};
     drop_graphs(b);
     return FV_OK;
@@ -637,7 +637,7 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
     const size_t bytes = (size_t)b->state_elems * elem_bytes(b->precision);
     std::vector<unsigned char> ref(bytes), got(bytes);
     const int warps[] = {1, 2, 4, 8, 16};
-    const int bps[] = {0, -1, 1, 2, 4};
+    const int bps[] = {0, -1, -2, 1, 2, 4};
     fv::FusedShape best{0, 0};
     float best_ms = 1e30f;
     bool have_ref = false;

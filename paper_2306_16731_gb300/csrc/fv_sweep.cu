@@ -346,6 +346,125 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
     __syncwarp();
 }
 
+
+// Row-sweep carries of one lane: the previous row's state, y flux and
+// eigenvalue, its x-face difference and the y face below it.
+template <typename C> struct Row2 {
+    C qp[4], Fyp[4], lyp, dxp[4], Fylp[4];
+};
+
+// Lower halo row: only F_y and lambda_y are needed.
+template <typename C>
+__device__ __forceinline__ void row2_lower_halo(Row2<C> &st, const C (&q0)[4], Gas<C> g)
+{
+    yphys(q0, g, st.Fyp, st.lyp);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) st.qp[k] = q0[k];
+}
+
+// Interior row y of the own column: physics, the y face below (which closes
+// row y-1: update, store, eigenvalue), the x faces (right face from the
+// right lane's volume, left face from the left lane, boundary faces from the
+// boundary pass), then row y becomes the carry.
+template <typename S, typename C>
+__device__ __forceinline__ void row2_interior(Row2<C> &st, const C (&q0)[4], Gas<C> g, int y, int P, int x,
+                                              C sc, bool active, bool fixed, S *dst, const C *bf,
+                                              const C *hv_row, Health<C> &hl, C &lmax)
+{
+    constexpr int N = 4;
+    const int64_t RS = (int64_t)(P + 2) * N;
+    Prim<2, C> s = primitives<2>(q0, g);
+    C Fx[N], Fy[N];
+    flux<2>(q0, s, 0, Fx);
+    flux<2>(q0, s, 1, Fy);
+    const C lx = eigenvalue<2>(s, 0), ly = eigenvalue<2>(s, 1);
+
+    C Fyl[N];
+    rusanov2<N>(st.qp, q0, st.Fyp, Fy, st.lyp, ly, Fyl);
+    if (y > 0) {
+        C qn[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) qn[k] = st.qp[k] - sc * (st.dxp[k] + (Fyl[k] - st.Fylp[k]));
+        store_row_volume<N>(dst + y * RS, qn, active, fixed, x, P, hv_row + (y - 1) * 2 * N);
+        Prim<2, C> t = primitives<2>(qn, g);
+        const C l = max_eigenvalue<2>(t);
+        hl.add(qn[0], t.p, l);
+        lmax = fv_max(lmax, l);
+    }
+
+    C qr[N], Fr_[N], Fr[N], Fl[N];
+    shfl_down_vec<N>(q0, qr);
+    shfl_down_vec<N>(Fx, Fr_);
+    const C lr = __shfl_down_sync(0xffffffffu, lx, 1);
+    rusanov2<N>(q0, qr, Fx, Fr_, lx, lr, Fr);
+    if (x == P - 1) load_volume<N>(bf + (y * 2 + 1) * N, Fr);
+#pragma unroll
+    for (int k = 0; k < N; ++k) Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
+    if (x == 0) load_volume<N>(bf + (y * 2) * N, Fl);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        st.dxp[k] = Fr[k] - Fl[k];
+        st.Fylp[k] = Fyl[k];
+        st.qp[k] = q0[k];
+        st.Fyp[k] = Fy[k];
+    }
+    st.lyp = ly;
+}
+
+// Upper halo row: its y face closes row P-1.
+template <typename S, typename C>
+__device__ __forceinline__ void row2_upper_halo(Row2<C> &st, const C (&q0)[4], Gas<C> g, int P, int x, C sc,
+                                                bool active, bool fixed, S *dst, const C *hv_row,
+                                                Health<C> &hl, C &lmax)
+{
+    constexpr int N = 4;
+    const int64_t RS = (int64_t)(P + 2) * N;
+    C Fy[N], ly, Fyu[N];
+    yphys(q0, g, Fy, ly);
+    rusanov2<N>(st.qp, q0, st.Fyp, Fy, st.lyp, ly, Fyu);
+    C qn[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) qn[k] = st.qp[k] - sc * (st.dxp[k] + (Fyu[k] - st.Fylp[k]));
+    store_row_volume<N>(dst + P * RS, qn, active, fixed, x, P, hv_row + (P - 1) * 2 * N);
+    Prim<2, C> t = primitives<2>(qn, g);
+    const C l = max_eigenvalue<2>(t);
+    hl.add(qn[0], t.p, l);
+    lmax = fv_max(lmax, l);
+}
+
+// Boundary x faces (and halo volumes) of one packed face slot from the two
+// volumes adjacent to it.
+template <typename C>
+__device__ __forceinline__ void boundary_face2(const C (&qL)[4], const C (&qR)[4], Gas<C> g, int side,
+                                               C *bface_slot, C *hvol_slot)
+{
+    constexpr int N = 4;
+    C FL[N], FR[N], Fh[N], lL, lR;
+    xphys(qL, g, FL, lL);
+    xphys(qR, g, FR, lR);
+    rusanov2<N>(qL, qR, FL, FR, lL, lR, Fh);
+    store_volume<N>(bface_slot, Fh);
+    store_volume<N>(hvol_slot, side ? qR : qL);
+}
+
+// Per-patch maximum eigenvalue and next time step (lanes of a patch slot
+// reduce through shared memory; one lane per patch writes).
+template <typename C>
+__device__ __forceinline__ void patch_lambda2(const SweepParams &sp, C lmax, int lane, int x, int P, bool active,
+                                              int i, double h, C *red)
+{
+    red[lane] = lmax;
+    __syncwarp();
+    if (active && x == 0 && (sp.lambda_out || sp.dt_next_out)) {
+        C m = red[lane];
+        for (int j = 1; j < P; ++j) m = fv_max(m, red[lane + j]);
+        const double l = double(m);
+        if (sp.lambda_out) sp.lambda_out[i] = l;
+        if (sp.dt_next_out) sp.dt_next_out[i] = cfl_dt(sp.cfl, h, 2, l);
+    }
+    __syncwarp();
+}
+
 // Compile-time edge P (32/P patches per warp): rows stream through a
 // per-warp shared-memory ring of R rows filled by cp.async, R-1 rows ahead
 // of the row being computed, so many loads are in flight without holding
@@ -427,71 +546,23 @@ __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem
         load_volume<N>(reinterpret_cast<const S *>(rlane + ((y + 1) % R) * 32 * VB), qv);
     };
 
-    C qp[N], Fyp[N], lyp, dxp[N], Fylp[N];
+    Row2<C> st;
     C lmax = C(0);
     {
         C q0[N];
         advance(-1, q0);
-        yphys(q0, g, Fyp, lyp);
-#pragma unroll
-        for (int k = 0; k < N; ++k) qp[k] = q0[k];
+        row2_lower_halo(st, q0, g);
     }
-
 #pragma unroll 2
     for (int y = 0; y < P; ++y) {
         C q0[N];
         advance(y, q0);
-        Prim<2, C> s = primitives<2>(q0, g);
-        C Fx[N], Fy[N];
-        flux<2>(q0, s, 0, Fx);
-        flux<2>(q0, s, 1, Fy);
-        const C lx = eigenvalue<2>(s, 0), ly = eigenvalue<2>(s, 1);
-
-        C Fyl[N];
-        rusanov2<N>(qp, q0, Fyp, Fy, lyp, ly, Fyl);
-        if (y > 0) {
-            C qn[N];
-#pragma unroll
-            for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxp[k] + (Fyl[k] - Fylp[k]));
-            store_row_volume<N>(dst + y * RS, qn, active, !periodic, x, P, hv_row + (y - 1) * 2 * N);
-            Prim<2, C> t = primitives<2>(qn, g);
-            const C l = max_eigenvalue<2>(t);
-            hl.add(qn[0], t.p, l);
-            lmax = fv_max(lmax, l);
-        }
-
-        C qr[N], Fr_[N], Fr[N], Fl[N];
-        shfl_down_vec<N>(q0, qr);
-        shfl_down_vec<N>(Fx, Fr_);
-        const C lr = __shfl_down_sync(0xffffffffu, lx, 1);
-        rusanov2<N>(q0, qr, Fx, Fr_, lx, lr, Fr);
-        if (x == P - 1) load_volume<N>(bf + (y * 2 + 1) * N, Fr);
-#pragma unroll
-        for (int k = 0; k < N; ++k) Fl[k] = __shfl_up_sync(0xffffffffu, Fr[k], 1);
-        if (x == 0) load_volume<N>(bf + (y * 2) * N, Fl);
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            dxp[k] = Fr[k] - Fl[k];
-            Fylp[k] = Fyl[k];
-            qp[k] = q0[k];
-            Fyp[k] = Fy[k];
-        }
-        lyp = ly;
+        row2_interior<S>(st, q0, g, y, P, x, sc, active, !periodic, dst, bf, hv_row, hl, lmax);
     }
-
     {
-        C q0[N], Fy[N], ly, Fyu[N];
+        C q0[N];
         advance(P, q0);
-        yphys(q0, g, Fy, ly);
-        rusanov2<N>(qp, q0, Fyp, Fy, lyp, ly, Fyu);
-        C qn[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxp[k] + (Fyu[k] - Fylp[k]));
-        store_row_volume<N>(dst + P * RS, qn, active, !periodic, x, P, hv_row + (P - 1) * 2 * N);
-        Prim<2, C> t = primitives<2>(qn, g);
-        const C l = max_eigenvalue<2>(t);
-        hl.add(qn[0], t.p, l);
-        lmax = fv_max(lmax, l);
+        row2_upper_halo<S>(st, q0, g, P, x, sc, active, !periodic, dst, hv_row, hl, lmax);
     }
     cp_async_wait<0>();
 
@@ -562,6 +633,201 @@ __global__ void __launch_bounds__(FV_SWEEP_MAXT, FV_SWEEP_MINB) k_sweep2d(SweepP
     if (__any_sync(0xffffffffu, hl.bad()) && lane == 0) atomicOr(sp.b.flags, FV_FLAG_NONPHYSICAL);
 }
 
+
+// ---------------------------------------------------------------------------
+// Streaming variant for uniform batches: persistent warps take items
+// round-robin (item = warp + j * warps), and the row ring runs across item
+// boundaries, so the next item's rows -- and the volumes its boundary pass
+// needs, staged by cp.async one item ahead -- are in flight while the
+// current item finishes.  Same arithmetic as sweep2d_tpl.
+constexpr int kRingS = 6;
+
+template <typename S>
+__host__ __device__ constexpr int warp_smem_bytes2d_stream()
+{
+    using C = typename StorageTraits<S>::Compute;
+    return (2 * 64 * 4 + 32) * (int)sizeof(C) + (kRingS + 4) * 32 * 4 * (int)sizeof(S);
+}
+
+// cp.async the two volumes of each of this lane's (at most two) boundary
+// face slots of item k into the staging area.
+template <typename S, int P>
+__device__ __forceinline__ void stage_boundary2(const SweepParams &sp, int k, int lane, unsigned stage_s)
+{
+    constexpr int N = 4, E = P + 2, K = 32 / P, VB = 4 * (int)sizeof(S);
+    const S *q = static_cast<const S *>(sp.q_in);
+    const bool periodic = sp.b.halo_mode == 1;
+    const int cnt = min(K, sp.b.num_patches - k * K);
+    const int nf = 2 * P * cnt;
+#pragma unroll
+    for (int fi = 0; fi < 2; ++fi) {
+        const int f = lane + 32 * fi;
+        if (f < nf) {
+            const int fs = f / (2 * P), r = f - fs * 2 * P;
+            const int yy = r >> 1, side = r & 1;
+            int xl = side ? P - 1 : -1, xr = side ? P : 0;
+            if (periodic) { xl = wrap(xl, P); xr = wrap(xr, P); }
+            const S *ps = q + (int64_t)(k * K + fs) * sp.uniform_elems + (yy + 1) * E * N;
+            copy_volume4_async<S>(stage_s + ((fi * 2 + 0) * 32 + lane) * VB, ps + (xl + 1) * N);
+            copy_volume4_async<S>(stage_s + ((fi * 2 + 1) * 32 + lane) * VB, ps + (xr + 1) * N);
+        }
+    }
+}
+
+// Boundary pass of item k from the staged volumes (each lane reads only what
+// it staged itself).
+template <typename S, typename C, int P>
+__device__ __forceinline__ void boundary_from_stage2(const SweepParams &sp, int k, int lane,
+                                                     const unsigned char *stage, C *bface, C *hvol, Gas<C> g)
+{
+    constexpr int N = 4, K = 32 / P, VB = 4 * (int)sizeof(S);
+    const int cnt = min(K, sp.b.num_patches - k * K);
+    const int nf = 2 * P * cnt;
+#pragma unroll
+    for (int fi = 0; fi < 2; ++fi) {
+        const int f = lane + 32 * fi;
+        if (f < nf) {
+            const int fs = f / (2 * P), r = f - fs * 2 * P;
+            const int yy = r >> 1, side = r & 1;
+            C qL[N], qR[N];
+            load_volume<N>(reinterpret_cast<const S *>(stage + ((fi * 2 + 0) * 32 + lane) * VB), qL);
+            load_volume<N>(reinterpret_cast<const S *>(stage + ((fi * 2 + 1) * 32 + lane) * VB), qR);
+            boundary_face2(qL, qR, g, side, bface + ((fs * P + yy) * 2 + side) * N,
+                           hvol + ((fs * P + yy) * 2 + side) * N);
+        }
+    }
+}
+
+template <typename S, typename C, int P>
+__device__ __forceinline__ void sweep2d_stream(const SweepParams sp, int gw, int W, int lane,
+                                               C *__restrict__ bface, C *__restrict__ hvol,
+                                               C *__restrict__ red, unsigned char *__restrict__ ring,
+                                               unsigned char *__restrict__ stage, Health<C> &hl)
+{
+    constexpr int N = 4, E = P + 2, K = 32 / P, R = kRingS, RPI = P + 2;
+    constexpr int VB = 4 * (int)sizeof(S);
+    constexpr int RS = E * N;
+    const int nitems = sp.num_items;
+    if (gw >= nitems) return;
+    const int n_my = (nitems - gw + W - 1) / W;
+    const int total_rows = n_my * RPI;
+    const Gas<C> g = gas_of<C>(sp);
+    const S *__restrict__ q = static_cast<const S *>(sp.q_in);
+    S *__restrict__ qo = static_cast<S *>(sp.q_out);
+    const bool periodic = sp.b.halo_mode == 1;
+    const int T = sp.b.num_patches;
+    const int sub = lane / P, x = lane - sub * P;
+    const unsigned rbase = smem_u32(ring) + lane * VB, sbase = smem_u32(stage);
+    const unsigned char *rlane = ring + lane * VB;
+
+    // stream position t -> (item j of this warp, row y); issue its row
+    auto issue = [&](int t) {
+        if (t < total_rows) {
+            const int j = t / RPI, y = t - j * RPI - 1;
+            const int k = gw + j * W;
+            const int cnt = min(K, T - k * K);
+            const int slot = sub < cnt ? sub : 0;
+            const int yy = periodic ? wrap(y, P) : y;
+            const S *src = q + (int64_t)(k * K + slot) * sp.uniform_elems + (x + 1) * N + (yy + 1) * RS;
+            copy_volume4_async<S>(rbase + (t % R) * 32 * VB, src);
+        }
+    };
+    auto advance = [&](int t, C (&qv)[N]) {
+        issue(t + R - 1);
+        cp_async_commit();
+        cp_async_wait<R - 1>();
+        load_volume<N>(reinterpret_cast<const S *>(rlane + (t % R) * 32 * VB), qv);
+    };
+
+    stage_boundary2<S, P>(sp, gw, lane, sbase);               // joins the first row's group
+#pragma unroll
+    for (int t = 0; t < R - 1; ++t) {
+        issue(t);
+        cp_async_commit();
+    }
+    cp_async_wait<R - 2>();                                    // the first group has landed
+
+    for (int j = 0; j < n_my; ++j) {
+        const int k = gw + j * W;
+        const int cnt = min(K, T - k * K);
+        const bool active = sub < cnt;
+        const int slot = active ? sub : 0;
+        const int i = k * K + slot;
+        boundary_from_stage2<S, C, P>(sp, k, lane, stage, bface, hvol, g);
+        __syncwarp();
+        // staged volumes consumed: stage the next item's (they join the
+        // group of the next row issue and land one item ahead)
+        if (j + 1 < n_my) stage_boundary2<S, P>(sp, k + W, lane, sbase);
+
+        const int64_t base = (int64_t)i * sp.uniform_elems;
+        S *dst = qo + base + (x + 1) * N;
+        const double h = __ldg(sp.dx + i);
+        const C sc = half_step_ratio<C>(__ldg(sp.dt + i), h);
+        const C *bf = bface + (slot * P) * 2 * N;
+        const C *hv_row = hvol + (slot * P) * 2 * N;
+        const int t0 = j * RPI;
+
+        Row2<C> st;
+        C lmax = C(0);
+        {
+            C q0[N];
+            advance(t0, q0);
+            row2_lower_halo(st, q0, g);
+        }
+#pragma unroll 2
+        for (int y = 0; y < P; ++y) {
+            C q0[N];
+            advance(t0 + 1 + y, q0);
+            row2_interior<S>(st, q0, g, y, P, x, sc, active, !periodic, dst, bf, hv_row, hl, lmax);
+        }
+        {
+            C q0[N];
+            advance(t0 + P + 1, q0);
+            row2_upper_halo<S>(st, q0, g, P, x, sc, active, !periodic, dst, hv_row, hl, lmax);
+        }
+        patch_lambda2(sp, lmax, lane, x, P, active, i, h, red);
+    }
+    cp_async_wait<0>();
+}
+
+template <typename S, int P>
+__global__ void __launch_bounds__(FV_SWEEP_MAXT, FV_SWEEP_MINB) k_sweep2d_stream(SweepParams sp)
+{
+    using C = typename StorageTraits<S>::Compute;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wbase = smem_raw + warp * warp_smem_bytes2d_stream<S>();
+    C *bface = reinterpret_cast<C *>(wbase);
+    C *hvol = bface + 64 * 4;
+    C *red = hvol + 64 * 4;
+    unsigned char *ring = wbase + (2 * 64 * 4 + 32) * sizeof(C);
+    unsigned char *stage = ring + kRingS * 32 * 4 * sizeof(S);
+    Health<C> hl;
+    const int wpb = blockDim.x >> 5;
+    sweep2d_stream<S, C, P>(sp, blockIdx.x * wpb + warp, gridDim.x * wpb, lane, bface, hvol, red, ring, stage, hl);
+    if (__any_sync(0xffffffffu, hl.bad()) && lane == 0) atomicOr(sp.b.flags, FV_FLAG_NONPHYSICAL);
+}
+
+template <typename S, int P>
+cudaError_t launch_stream(const SweepParams &sp, int wpb, cudaStream_t st)
+{
+    static bool attr_set = false;
+    const int bytes = wpb * warp_smem_bytes2d_stream<S>();
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep2d_stream<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kMaxWarpsPerBlock * warp_smem_bytes2d_stream<S>());
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep2d_stream<S, P>, wpb * 32, bytes);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    int grid = std::min((sp.num_items + wpb - 1) / wpb, per_sm * num_sms());
+    if (grid < 1) grid = 1;
+    k_sweep2d_stream<S, P><<<grid, wpb * 32, bytes, st>>>(sp);
+    return cudaGetLastError();
+}
+
 // Grid: one warp per item, or (persistent) blocks_per_sm blocks per SM,
 // where blocks_per_sm < 0 means as many as can be resident at once.
 template <typename S, int P>
@@ -593,6 +859,15 @@ cudaError_t launch_class(const SweepParams &sp, int wpb, int bps, cudaStream_t s
 template <typename S>
 cudaError_t launch_class_p(int p, const SweepParams &sp, int wpb, int bps, cudaStream_t st)
 {
+    if (bps == -2 && sp.uniform_elems) {       // streaming persistent warps (uniform batches)
+        switch (p) {
+        case 8: return launch_stream<S, 8>(sp, wpb, st);
+        case 16: return launch_stream<S, 16>(sp, wpb, st);
+        case 32: return launch_stream<S, 32>(sp, wpb, st);
+        default: break;
+        }
+        bps = -1;
+    }
     switch (p) {
     case 4: return launch_class<S, 4>(sp, wpb, bps, st);
     case 8: return launch_class<S, 8>(sp, wpb, bps, st);
@@ -647,7 +922,7 @@ cudaError_t launch_fused_update(const BatchView &b, int precision, const StepArg
     int wpb = plan.shape.warps_per_block;
     if (wpb < 1) wpb = 1;
     if (wpb > kMaxWarpsPerBlock) wpb = kMaxWarpsPerBlock;
-    sp.persistent = plan.shape.blocks_per_sm != 0;
+    sp.persistent = plan.shape.blocks_per_sm != 0;      // -1 and -2 are persistent too
     for (int c = 0; c < plan.num_classes; ++c) {
         sp.item_begin = plan.class_begin[c];
         sp.num_items = plan.class_end[c] - plan.class_begin[c];

@@ -316,3 +316,41 @@ def test_invalid_device_arguments():
         b.set_form(9)
     assert ei.value.code == fb.FV_EINVAL
     b.close()
+
+
+@pytest.mark.parametrize("p,T", [(16, 3001), (8, 1500), (32, 700), (4, 900)])
+def test_launch_shapes_are_bitwise_identical(p, T):
+    """Every launch shape the tuner can pick (one warp per item, counter-fed
+    persistent warps, round-robin streaming warps) computes the same bits."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(2, [p] * T, seed=40 + p, dx=0.02, dtype=np.float32)
+    results = []
+    for shape in [(4, 0), (2, -1), (4, -2), (1, -2), (8, 1), (16, 0)]:
+        b = fb.FVBatch(2, w.patch_size, precision=fb.FV_F32)
+        b.set_launch_shape(*shape)
+        qa = torch.from_numpy(w.Q0).cuda()
+        qb = qa.clone()
+        dx = torch.tensor(w.dx, device="cuda")
+        lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+        dta, dtb = torch.zeros_like(lam), torch.zeros_like(lam)
+        b.max_eigenvalue(qa, lam)
+        b.cfl_time_step(lam, dx, 0.4, dta)
+        b.run(qa, qb, dx, dta, dtb, lam, 5, 0.4, use_graph=shape[1] == -2)
+        b.status()
+        results.append((qb.cpu().numpy(), lam.cpu().numpy()))
+        b.close()
+    for q, l in results[1:]:
+        assert np.array_equal(q, results[0][0]) and np.array_equal(l, results[0][1])
+    # and the result is right
+    ref, _, _ = oracle.batch_run(2, w.patch_size, w.dx, w.Q0.astype(np.float64), 5)
+    assert batch_rel_linf(results[0][0], ref, 2, w.patch_size) < 1e-5
+
+
+def test_tuner_picks_a_shape_and_keeps_results(tmp_path, monkeypatch):
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.config(2, num_patches=2000, dtype=np.float32)
+    a = gpu_run(w, 1, 0, 6, tune=False)
+    b = gpu_run(w, 1, 0, 6, tune=True)
+    assert np.array_equal(a[0], b[0])

@@ -28,6 +28,7 @@ namespace fv {
 namespace {
 
 constexpr int kRing3 = 4;     // planes in the ring
+
 constexpr int kMaxThreads3 = 256;    // p <= 16: one thread per (x, y) column
 
 // Register budget: three 256-thread blocks per SM in float (80 registers),
@@ -691,6 +692,7 @@ cudaError_t launch3b(const Sweep3Params &sp, int chunk, cudaStream_t st, int pre
     k_sweep3d_b8<S, C><<<sp.count, threads, smem, st>>>(sp, plane_bytes, std::min(chunk, pow2_align(plane_bytes)));
     return cudaGetLastError();
 }
+
 
 }  // namespace
 

@@ -354,3 +354,46 @@ def test_tuner_picks_a_shape_and_keeps_results(tmp_path, monkeypatch):
     a = gpu_run(w, 1, 0, 6, tune=False)
     b = gpu_run(w, 1, 0, 6, tune=True)
     assert np.array_equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("p,T", [(8, 300), (16, 40)])
+def test_3d_block_kernel_periodic_conservation_and_graph(p, T):
+    """The 8x8-block 3D kernel (uniform edge multiple of 8): periodic patches
+    conserve their totals to round-off, graph replay equals eager launches
+    bitwise, and the state matches the oracle."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(3, [p] * T, seed=60 + p, halo_mode=inputs.PERIODIC, dtype=np.float32)
+    eager = gpu_run(w, 1, 0, 6, use_graph=False)
+    graph = gpu_run(w, 1, 0, 6, use_graph=True)
+    assert "sweep3d" in eager[3]
+    assert np.array_equal(eager[0], graph[0]) and np.array_equal(eager[1], graph[1])
+    ref, _, _ = oracle.batch_run(3, w.patch_size, w.dx, initial_fp64(w.Q0, 1), 6, halo_mode=inputs.PERIODIC)
+    assert batch_rel_linf(eager[0], ref, 3, w.patch_size) < 1e-5
+    b = fb.FVBatch(3, w.patch_size, precision=0, halo_mode=inputs.PERIODIC)
+    t0 = torch.zeros(T * 5, dtype=torch.float64, device="cuda")
+    t1 = torch.zeros_like(t0)
+    b.conserved_totals(torch.from_numpy(initial_fp64(w.Q0, 1)).cuda(), t0)
+    b.conserved_totals(torch.from_numpy(eager[0]).cuda(), t1)
+    torch.cuda.synchronize()
+    mag = oracle.batch_totals(3, w.patch_size, np.abs(initial_fp64(w.Q0, 1))).reshape(-1)
+    # FP32 arithmetic: a few float ulps of each volume's magnitude per step
+    bound = 6 * 8 * np.finfo(np.float32).eps * mag + 1e-12
+    assert np.all(np.abs(t1.cpu().numpy() - t0.cpu().numpy()) <= bound)
+    b.close()
+
+
+@pytest.mark.parametrize("dim,p", [(2, 16), (2, 8), (3, 8)])
+def test_bfloat16_storage_error_is_stated_and_bounded(dim, p):
+    w = inputs.uniform_batch(dim, [p] * 64, seed=70 + p, dx=0.02)
+    got, lam, dtn, desc = gpu_run(w, 2, 0, 10)
+    ref, lam_ref, _ = oracle.batch_run(dim, w.patch_size, w.dx, initial_fp64(w.Q0, 2), 10)
+    err = batch_rel_linf(got, ref, dim, w.patch_size)
+    print("bf16 storage dim %d p %d: rel Linf after 10 steps %.3e (%s)" % (dim, p, err, desc))
+    assert err < 5e-2
+
+
+def test_uneven_3d_batch_mixes_kernels_correctly():
+    w = inputs.uniform_batch(3, [8, 4, 8, 6, 3, 8, 5], seed=80, dx=np.linspace(0.05, 0.1, 7))
+    for precision in (0, 1):
+        _check(w, precision, FORMS["fused"], 5)

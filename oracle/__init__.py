@@ -13,6 +13,7 @@ from .fv_oracle import (  # noqa: F401
     cfl_time_step,
     batch_run,
     batch_totals,
+    halo_exchange,
     num_threads,
     FIXED,
     PERIODIC,

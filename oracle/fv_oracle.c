@@ -404,3 +404,53 @@ int fvo_num_threads(void)
     return 1;
 #endif
 }
+
+/* Halo fill from neighbouring patches (the step before the kernel call in
+ * the paper's framework: patches are equipped with a halo layer of width one
+ * taken from their neighbours, Sec. 2.2).  nbr has 2*dim entries per patch in
+ * the order -x, +x, -y, +y[, -z, +z]: the index of the patch across that face
+ * (same edge length), or -1 to leave that face's halo as it is.  For each
+ * face with a neighbour, every face-halo volume (corners excluded) receives
+ * the neighbour's interior volume that touches the face: across -x the
+ * neighbour's column x = p-1, across +x its column x = 0, and likewise in y
+ * and z.  Q is updated in place (only halo volumes are written). */
+int fvo_halo_exchange(int dim, int T, const int32_t *p, const int32_t *nbr, double *Q)
+{
+    int rc = check_batch(dim, T, p);
+    if (rc) return rc;
+    for (int i = 0; i < T * 2 * dim; ++i) {
+        int j = nbr[i];
+        if (j < -1 || j >= T || (j >= 0 && p[j] != p[i / (2 * dim)])) return FVO_EINVAL;
+    }
+    int64_t *off = patch_offsets(dim, T, p);
+    if (!off) return FVO_ENOMEM;
+    int N = dim + 2;
+    for (int i = 0; i < T; ++i) {
+        int P = p[i];
+        int kmax = dim == 3 ? P - 1 : 0;
+        for (int face = 0; face < 2 * dim; ++face) {
+            int j = nbr[i * 2 * dim + face];
+            if (j < 0) continue;
+            int axis = face / 2, upper = face % 2;
+            /* halo coordinate along the axis and the neighbour's source index */
+            int dst_a = upper ? P : -1, src_a = upper ? 0 : P - 1;
+            for (int k = 0; k <= kmax; ++k)
+                for (int t = 0; t < P; ++t) {
+                    int dc[3], sc[3];
+                    /* the two tangential coordinates run over the interior */
+                    int tan[2] = {t, k};
+                    int ti = 0;
+                    for (int a = 0; a < dim; ++a) {
+                        if (a == axis) { dc[a] = dst_a; sc[a] = src_a; }
+                        else { dc[a] = tan[ti]; sc[a] = tan[ti]; ++ti; }
+                    }
+                    if (dim == 2) { dc[2] = 0; sc[2] = 0; }
+                    int64_t d = off[i] + cell_index(dim, P, dc[0], dc[1], dc[2]) * N;
+                    int64_t s = off[j] + cell_index(dim, P, sc[0], sc[1], sc[2]) * N;
+                    for (int q = 0; q < N; ++q) Q[d + q] = Q[s + q];
+                }
+        }
+    }
+    free(off);
+    return FVO_OK;
+}

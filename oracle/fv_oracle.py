@@ -72,6 +72,8 @@ def bind(path: str):
                                   ctypes.c_int, _dp, _dp, _dp]
     lib.fvo_batch_totals.restype = ctypes.c_int
     lib.fvo_batch_totals.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, _dp]
+    lib.fvo_halo_exchange.restype = ctypes.c_int
+    lib.fvo_halo_exchange.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp]
     lib.fvo_num_threads.restype = ctypes.c_int
     lib.fvo_num_threads.argtypes = []
     return lib
@@ -203,6 +205,18 @@ def batch_totals(dim, patch_size, Q):
     out = np.empty(len(p) * (dim + 2), dtype=np.float64)
     _check(lib.fvo_batch_totals(dim, len(p), _ptr_i(p), _ptr_d(Q), _ptr_d(out)), "totals")
     return out.reshape(len(p), dim + 2)
+
+
+def halo_exchange(dim, patch_size, neighbours, Q):
+    """Copy of Q with every face halo that has a neighbour filled from the
+    neighbour's interior (neighbours: [T, 2*dim], order -x,+x,-y,+y[,-z,+z],
+    -1 = keep)."""
+    lib = _load()
+    p = _i32(patch_size)
+    nb = _i32(neighbours)
+    Q = _f64(Q).copy()
+    _check(lib.fvo_halo_exchange(dim, len(p), _ptr_i(p), _ptr_i(nb), _ptr_d(Q)), "halo_exchange")
+    return Q
 
 
 def num_threads() -> int:

@@ -119,6 +119,28 @@ int fv_batch_set_form(fv_batch_t *b, int form);
  * arithmetic). */
 int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per_sm);
 
+/*
+ * Register which patch lies across each face (the halo layer of width one
+ * that the paper's framework fills from neighbouring patches before the
+ * kernel call, Sec. 2.2).  neighbours is a HOST array of num_patches * 2 *
+ * dim entries in the order -x, +x, -y, +y[, -z, +z]: the index of the patch
+ * across that face (it must have the same edge length), or -1 for a face
+ * whose halo is taken from the patch itself (the halo mode).  NULL clears
+ * the table.  Copied to the device (allocates once; FV_ENOMEM).  With a
+ * table registered, fv_halo_exchange fills face halos from neighbours, the
+ * fused 2D kernels for edge lengths 4, 8, 16 and 32 read the neighbours'
+ * edge volumes directly in fv_patch_batch_update (no exchange needed), and
+ * fv_batch_run runs an exchange before each update for every other kernel.
+ */
+int fv_batch_set_neighbours(fv_batch_t *b, const int32_t *neighbours);
+
+/* Fill every face-halo volume that has a neighbour with the neighbour's
+ * interior volume touching that face (across -x its column p-1, across +x
+ * its column 0, likewise in y and z), in place on the device state Q;
+ * corner and edge halo volumes are not written.  Asynchronous on the
+ * batch's stream.  FV_EINVAL without a registered table. */
+int fv_halo_exchange(fv_batch_t *b, void *Q);
+
 /* Rebind the batch to another stream (e.g. a capture stream). */
 int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream);
 

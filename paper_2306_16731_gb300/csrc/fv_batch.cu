@@ -85,6 +85,8 @@ struct fv_batch {
     std::vector<fv::WorkItem> items_h;
 
     std::map<GraphKey, cudaGraphExec_t> graphs;
+
+    int32_t *nbr = nullptr;            // device neighbour table (fv_batch_set_neighbours)
 };
 
 namespace fv {
@@ -366,6 +368,57 @@ int fv_batch_set_form(fv_batch_t *b, int form)
     return FV_OK;
 }
 
+int fv_batch_set_neighbours(fv_batch_t *b, const int32_t *neighbours)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    if (!neighbours) {
+        if (b->nbr) cudaFree(b->nbr);
+        b->nbr = nullptr;
+        b->view.nbr = nullptr;
+        drop_graphs(b);
+        return FV_OK;
+    }
+    const int faces = 2 * b->dim;
+    for (int i = 0; i < b->T; ++i)
+        for (int f = 0; f < faces; ++f) {
+            const int j = neighbours[(size_t)i * faces + f];
+            if (j < -1 || j >= b->T)
+                return fail(FV_EINVAL, "patch %d face %d: neighbour %d out of range", i, f, j);
+            if (j >= 0 && b->psize[j] != b->psize[i])
+                return fail(FV_EINVAL, "patch %d face %d: neighbour %d has edge %d, not %d", i, f, j, b->psize[j],
+                            b->psize[i]);
+        }
+    const size_t bytes = (size_t)b->T * faces * sizeof(int32_t);
+    if (!b->nbr && bytes) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FV_ENOMEM, "neighbour table: %s", cudaGetErrorString(e));
+        }
+        b->nbr = static_cast<int32_t *>(p);
+    }
+    if (bytes) {
+        cudaError_t e = cudaMemcpy(b->nbr, neighbours, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "neighbour table upload");
+    }
+    b->view.nbr = b->nbr;
+    drop_graphs(b);
+    return FV_OK;
+}
+
+int fv_halo_exchange(fv_batch_t *b, void *Q)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (b->T == 0) return FV_OK;
+    if (!b->view.nbr) return fail(FV_EINVAL, "no neighbour table registered (fv_batch_set_neighbours)");
+    if (!Q) return fail(FV_EINVAL, "state pointer is NULL");
+    DeviceGuard dg(b->device);
+    cudaError_t e = fv::launch_halo_exchange(b->view, b->precision, b->view.nbr, Q, b->stream);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "halo exchange launch");
+}
+
 int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per_sm)
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
@@ -463,6 +516,10 @@ static int enqueue_steps(fv_batch_t *b, cudaStream_t st, void *Q_a, void *Q_b, c
         const double *dti = (s & 1) ? dt_b : dt_a;
         double *dto = (s & 1) ? dt_a : dt_b;
         double *lam = (s == steps - 1) ? lambda_out : nullptr;
+        if (b->view.nbr && !(b->form == FV_FORM_FUSED && fv::fused_reads_neighbours(b->plan))) {
+            cudaError_t e = fv::launch_halo_exchange(b->view, b->precision, b->view.nbr, const_cast<void *>(qi), st);
+            if (e != cudaSuccess) return cuda_fail(e, "halo exchange launch");
+        }
         int rc = launch_update(b, st, qi, qo, dx, dti, lam, dto, cfl);
         if (rc) return rc;
     }
@@ -531,6 +588,7 @@ int fv_batch_destroy(fv_batch_t *b)
     drop_graphs(b);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     if (b->scratch) cudaFree(b->scratch);
+    if (b->nbr) cudaFree(b->nbr);
     if (b->meta) cudaFree(b->meta);
     delete b;
     return FV_OK;
@@ -546,7 +604,7 @@ int fv_batch_launches_per_update(const fv_batch_t *b)
     switch (b->form) {
     case FV_FORM_CASCADE: return 5;
     case FV_FORM_TILE: return 1;
-    default: return b->plan.num_classes;   // one launch per patch-size class
+    default: return b->plan.num_classes;   // one launch per patch-size class (neighbours read in-kernel)
     }
 }
 

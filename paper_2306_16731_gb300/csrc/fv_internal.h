@@ -24,6 +24,7 @@ struct BatchView {
     int max_p;
     int uniform_p;             // p if all patches share it, else 0
     int align_bytes;           // largest power of two <= 16 dividing every patch's (and 3D plane's) bytes
+    const int32_t *nbr;        // [T][2 dim] neighbour across -x,+x,-y,+y[,-z,+z] or -1; null = none registered
 };
 
 // Arguments of one update.
@@ -94,6 +95,11 @@ cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepA
                                   const FusedPlan &plan, cudaStream_t st);
 int fused_items_for(int dim, int p, int *patches_per_item);
 
+cudaError_t launch_halo_exchange(const BatchView &b, int precision, const int32_t *nbr, void *q,
+                                 cudaStream_t st);
+// true if the fused kernel chosen for this plan reads neighbours' volumes
+// itself (so an update needs no separate exchange)
+bool fused_reads_neighbours(const FusedPlan &plan);
 cudaError_t launch_max_eigenvalue(const BatchView &b, int precision, const void *q,
                                   double *lambda_out, cudaStream_t st);
 cudaError_t launch_cfl_time_step(const BatchView &b, const double *lambda, const double *dx,

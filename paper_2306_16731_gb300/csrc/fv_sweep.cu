@@ -118,6 +118,12 @@ template <> __device__ __forceinline__ void copy_volume4_async<__nv_bfloat16>(un
     cp_async_8(s, g);
 }
 
+// Element offset of patch i (arithmetic for uniform batches).
+__device__ __forceinline__ int64_t patch_base2(const SweepParams &sp, int i)
+{
+    return sp.uniform_elems ? (int64_t)i * sp.uniform_elems : __ldg(sp.b.elem_off + i);
+}
+
 template <typename C> __device__ __forceinline__ Gas<C> gas_of(const SweepParams &sp);
 template <> __device__ __forceinline__ Gas<float> gas_of<float>(const SweepParams &sp)
 {
@@ -497,14 +503,21 @@ __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem
     const unsigned rbase = smem_u32(ring) + lane * VB;
     const unsigned char *rlane = ring + lane * VB;
 
+    // the two halo rows: own halo memory, the wrapped interior (periodic) or
+    // the neighbour's edge row across y (neighbour table registered)
+    const S *row_lo = src + (periodic ? P : 0) * RS, *row_hi = src + (periodic ? 1 : P + 1) * RS;
+    if (sp.b.nbr) {
+        const int nlo = __ldg(sp.b.nbr + (int64_t)i * 4 + 2), nhi = __ldg(sp.b.nbr + (int64_t)i * 4 + 3);
+        if (nlo >= 0) row_lo = q + patch_base2(sp, nlo) + (x + 1) * N + P * RS;     // its row P-1
+        if (nhi >= 0) row_hi = q + patch_base2(sp, nhi) + (x + 1) * N + 1 * RS;     // its row 0
+    }
+    auto row_src = [&](int y) { return y < 0 ? row_lo : (y >= P ? row_hi : src + (y + 1) * RS); };
+
     // rows -1 .. R-3 in flight before anything else
 #pragma unroll
     for (int r = 0; r < R - 1; ++r) {
         const int y = r - 1;
-        if (y <= P) {
-            const int yy = periodic ? wrap(y, P) : y;
-            copy_volume4_async<S>(rbase + ((y + 1) % R) * 32 * VB, src + (yy + 1) * RS);
-        }
+        if (y <= P) copy_volume4_async<S>(rbase + ((y + 1) % R) * 32 * VB, row_src(y));
         cp_async_commit();
     }
 
@@ -515,12 +528,21 @@ __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem
         const int r = f - fs * 2 * P;
         const int yy = r >> 1, side = r & 1;
         const int ip = sp.uniform_elems ? it.first_patch + fs : __ldg(sp.order + it.first_patch + fs);
-        const S *ps = q + (sp.uniform_elems ? (int64_t)ip * sp.uniform_elems : __ldg(sp.b.elem_off + ip));
+        const S *ps = q + patch_base2(sp, ip);
         int xl = side ? P - 1 : -1, xr = side ? P : 0;
         if (periodic) { xl = wrap(xl, P); xr = wrap(xr, P); }
+        const S *pl = ps + ((yy + 1) * E + (xl + 1)) * N, *pr = ps + ((yy + 1) * E + (xr + 1)) * N;
+        if (sp.b.nbr) {                        // the halo volume comes from the neighbour across x
+            const int n = __ldg(sp.b.nbr + (int64_t)ip * 4 + side);
+            if (n >= 0) {
+                const S *pn = q + patch_base2(sp, n) + (yy + 1) * E * N;
+                if (side) pr = pn + 1 * N;               // neighbour's column 0
+                else pl = pn + P * N;                    // neighbour's column P-1
+            }
+        }
         C qL[N], qR[N], FL[N], FR[N], Fh[N], lL, lR;
-        load_volume<N>(ps + ((yy + 1) * E + (xl + 1)) * N, qL);
-        load_volume<N>(ps + ((yy + 1) * E + (xr + 1)) * N, qR);
+        load_volume<N>(pl, qL);
+        load_volume<N>(pr, qR);
         xphys(qL, g, FL, lL);
         xphys(qR, g, FR, lR);
         rusanov2<N>(qL, qR, FL, FR, lL, lR, Fh);
@@ -537,10 +559,7 @@ __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem
     // issue row y+R-1, then wait until row y (ring slot (y+1) % R) has landed
     auto advance = [&](int y, C (&qv)[N]) {
         const int yn = y + R - 1;
-        if (yn <= P) {
-            const int yy = periodic ? wrap(yn, P) : yn;
-            copy_volume4_async<S>(rbase + ((yn + 1) % R) * 32 * VB, src + (yy + 1) * RS);
-        }
+        if (yn <= P) copy_volume4_async<S>(rbase + ((yn + 1) % R) * 32 * VB, row_src(yn));
         cp_async_commit();
         cp_async_wait<R - 1>();
         load_volume<N>(reinterpret_cast<const S *>(rlane + ((y + 1) % R) * 32 * VB), qv);
@@ -859,7 +878,7 @@ cudaError_t launch_class(const SweepParams &sp, int wpb, int bps, cudaStream_t s
 template <typename S>
 cudaError_t launch_class_p(int p, const SweepParams &sp, int wpb, int bps, cudaStream_t st)
 {
-    if (bps == -2 && sp.uniform_elems) {       // streaming persistent warps (uniform batches)
+    if (bps == -2 && sp.uniform_elems && !sp.b.nbr) {   // streaming persistent warps (uniform batches)
         switch (p) {
         case 8: return launch_stream<S, 8>(sp, wpb, st);
         case 16: return launch_stream<S, 16>(sp, wpb, st);
@@ -878,6 +897,16 @@ cudaError_t launch_class_p(int p, const SweepParams &sp, int wpb, int bps, cudaS
 }
 
 }  // namespace
+
+bool fused_reads_neighbours(const FusedPlan &plan)
+{
+    if (plan.kernel != FUSED_SWEEP2D) return false;
+    for (int c = 0; c < plan.num_classes; ++c) {
+        const int p = plan.class_p[c];
+        if (p != 4 && p != 8 && p != 16 && p != 32) return false;   // runtime-edge sweep reads own halos
+    }
+    return true;
+}
 
 bool fused_supported(const BatchView &b, int precision, int *kernel)
 {

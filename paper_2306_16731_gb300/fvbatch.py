@@ -38,6 +38,7 @@ _ERRNAMES = {FV_EINVAL: "FV_EINVAL", FV_ENOMEM: "FV_ENOMEM", FV_ECUDA: "FV_ECUDA
              FV_EUNSUPPORTED: "FV_EUNSUPPORTED", FV_ENONPHYSICAL: "FV_ENONPHYSICAL"}
 
 EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_batch_set_launch_shape",
+           "fv_batch_set_neighbours", "fv_halo_exchange",
            "fv_patch_batch_update", "fv_max_eigenvalue", "fv_cfl_time_step",
            "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
@@ -78,6 +79,8 @@ def load() -> ctypes.CDLL:
             "fv_batch_set_form": (i, [_vp, i]),
             "fv_batch_set_stream": (i, [_vp, _vp]),
             "fv_batch_set_launch_shape": (i, [_vp, i, i]),
+            "fv_batch_set_neighbours": (i, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+            "fv_halo_exchange": (i, [_vp, _vp]),
             "fv_patch_batch_update": (i, [_vp, _vp, _vp, _dp, _dp, _dp, _dp, d]),
             "fv_max_eigenvalue": (i, [_vp, _vp, _dp]),
             "fv_cfl_time_step": (i, [_vp, _dp, _dp, d, _dp]),
@@ -137,6 +140,19 @@ def fv_batch_create(dim, patch_size, halo=1, unknowns=None, precision=FV_F64,
 
 def fv_batch_set_form(b, form):
     return _check(load().fv_batch_set_form(b, int(form)))
+
+
+def fv_batch_set_neighbours(b, neighbours):
+    """neighbours: host ints [T, 2*dim] (order -x,+x,-y,+y[,-z,+z]; -1 = own halo) or None."""
+    if neighbours is None:
+        return _check(load().fv_batch_set_neighbours(b, None))
+    flat = [int(v) for row in neighbours for v in (row if hasattr(row, "__iter__") else [row])]
+    arr = (ctypes.c_int32 * max(1, len(flat)))(*flat)
+    return _check(load().fv_batch_set_neighbours(b, arr))
+
+
+def fv_halo_exchange(b, Q):
+    return _check(load().fv_halo_exchange(b, _addr(Q)))
 
 
 def fv_batch_set_launch_shape(b, warps_per_block, blocks_per_sm):
@@ -231,6 +247,12 @@ class FVBatch:
 
     def set_form(self, form):
         fv_batch_set_form(self.handle, form)
+
+    def set_neighbours(self, neighbours):
+        fv_batch_set_neighbours(self.handle, neighbours)
+
+    def halo_exchange(self, Q):
+        fv_halo_exchange(self.handle, Q)
 
     def set_launch_shape(self, warps_per_block, blocks_per_sm):
         fv_batch_set_launch_shape(self.handle, warps_per_block, blocks_per_sm)

@@ -21,7 +21,7 @@ import pytest
 import oracle
 from paper_2306_16731_gb300 import inputs
 from tests._helpers import batch_rel_linf, batch_rel_linf_components, patches_interior
-from tests.gpu_util import gpu_run, initial_fp64, subset, take_patches
+from tests.gpu_util import gpu_run, initial_fp64, subset, take_patches, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -397,3 +397,87 @@ def test_uneven_3d_batch_mixes_kernels_correctly():
     w = inputs.uniform_batch(3, [8, 4, 8, 6, 3, 8, 5], seed=80, dx=np.linspace(0.05, 0.1, 7))
     for precision in (0, 1):
         _check(w, precision, FORMS["fused"], 5)
+
+
+def _grid_neighbours(G, dim, open_faces=()):
+    from tests.test_oracle_halo_exchange import grid_neighbours
+    nb = grid_neighbours(G, dim)
+    for (i, f) in open_faces:
+        nb[i, f] = -1
+    return nb
+
+
+@pytest.mark.parametrize("dim,G,p,precision", [(2, 5, 8, 0), (2, 4, 16, 1), (3, 2, 8, 0), (3, 2, 6, 2)])
+def test_halo_exchange_is_bitwise_the_oracle_exchange(dim, G, p, precision):
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    T = G ** dim
+    w = inputs.uniform_batch(dim, [p] * T, seed=90 + dim)
+    nb = _grid_neighbours(G, dim, open_faces=[(0, 0), (1, 3)])
+    b = fb.FVBatch(dim, w.patch_size, precision=precision)
+    b.set_neighbours(nb.tolist())
+    q = to_device(w.Q0, precision)
+    b.halo_exchange(q)
+    torch.cuda.synchronize()
+    got = q.to(torch.float64).cpu().numpy()
+    want = oracle.halo_exchange(dim, w.patch_size, nb, initial_fp64(w.Q0, precision))
+    assert np.array_equal(got, want)
+    b.close()
+
+
+def _oracle_grid_run(w, nb, steps, precision):
+    Q = initial_fp64(w.Q0, precision)
+    lam = oracle.batch_max_eigenvalue(w.dim, w.patch_size, Q)
+    for _ in range(steps):
+        dt = oracle.cfl_time_step(w.dim, lam, w.dx, w.cfl)
+        Q = oracle.halo_exchange(w.dim, w.patch_size, nb, Q)
+        Q, lam = oracle.batch_step(w.dim, w.patch_size, w.dx, dt, Q, w.gamma, w.halo_mode)
+    return Q, lam
+
+
+@pytest.mark.parametrize("form", ["fused", "cascade", "tile"])
+@pytest.mark.parametrize("dim,G,p,precision", [(2, 6, 16, 0), (2, 4, 8, 1), (3, 2, 8, 0)])
+def test_patch_grid_with_neighbours_matches_oracle(form, dim, G, p, precision):
+    """Patches wired as a periodic grid (two faces left open to their own
+    halos): the fused 2D kernels read neighbours in-kernel, every other
+    kernel gets an exchange before each update inside fv_batch_run."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    T = G ** dim
+    w = inputs.uniform_batch(dim, [p] * T, seed=110 + dim + p, dx=np.linspace(0.01, 0.02, T))
+    nb = _grid_neighbours(G, dim, open_faces=[(0, 1), (T - 1, 2)])
+    if not _supported(w, precision, FORMS[form]):
+        pytest.skip("no kernel")
+    b = fb.FVBatch(dim, w.patch_size, precision=precision, form=FORMS[form])
+    b.set_neighbours(nb.tolist())
+    qa = to_device(w.Q0, precision)
+    qb = qa.clone()
+    dx = torch.tensor(w.dx, device="cuda")
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dta, dtb = torch.zeros_like(lam), torch.zeros_like(lam)
+    b.max_eigenvalue(qa, lam)
+    b.cfl_time_step(lam, dx, w.cfl, dta)
+    steps = 7
+    b.run(qa, qb, dx, dta, dtb, lam, steps, w.cfl, use_graph=True)
+    b.status()
+    got = (qb if steps % 2 else qa).to(torch.float64).cpu().numpy()
+    ref, lam_ref = _oracle_grid_run(w, nb, steps, precision)
+    err = batch_rel_linf(got, ref, dim, w.patch_size)
+    assert err <= TOL[precision], (err, b.describe())
+    assert np.max(np.abs(lam.cpu().numpy() - lam_ref) / lam_ref) <= TOL[precision]
+    b.close()
+
+
+def test_neighbour_table_is_validated():
+    from paper_2306_16731_gb300 import fvbatch as fb
+    b = fb.FVBatch(2, [4, 4, 8], precision=0)
+    for bad in ([[5, -1, -1, -1]] * 3, [[2, -1, -1, -1], [-1] * 4, [-1] * 4], [[-2, -1, -1, -1]] * 3):
+        with pytest.raises(fb.FVError) as ei:
+            b.set_neighbours(bad)
+        assert ei.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError):
+        import torch
+        b.halo_exchange(torch.zeros(8, device="cuda"))      # no table registered
+    b.set_neighbours([[1, -1, -1, -1], [-1, 0, -1, -1], [-1] * 4])
+    b.set_neighbours(None)
+    b.close()

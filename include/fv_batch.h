@@ -161,6 +161,26 @@ int fv_patch_batch_update(fv_batch_t *b, const void *Q_in, void *Q_out,
                           const double *dx, const double *dt,
                           double *lambda_out, double *dt_next_out, double cfl);
 
+/*
+ * One update of a batch whose state lives in HOST memory (the data
+ * movement that dominates the paper's end-to-end runtimes, Sec. 5 and
+ * Sec. 4 "Data transfer").  Q_in_host / Q_out_host are host state buffers
+ * (page-locked for full speed), dx_host / dt_host host arrays of
+ * num_patches doubles, lambda_host / dt_next_host optional host outputs.
+ * A uniform batch using the fused form is cut into `chunks` (1..64) ranges
+ * of patches whose host-to-device copies, updates and device-to-host copies
+ * run on three streams, so copies in both directions overlap each other and
+ * the updates; any other batch runs as one chunk.  The first call creates
+ * the device staging (two state buffers and four arrays of num_patches
+ * doubles) and two copy streams, kept until fv_batch_destroy (FV_ENOMEM).
+ * Synchronous: returns when Q_out_host and the outputs are complete.  The
+ * halo volumes of Q_out_host are unspecified.
+ */
+int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, void *Q_out_host,
+                               const double *dx_host, const double *dt_host,
+                               double *lambda_host, double *dt_next_host, double cfl,
+                               int chunks);
+
 /* Per-patch maximum eigenvalue of Q (Sec. 2.2, Sec. 4 "Reduction"):
  * lambda_out[i] = max over interior volumes and directions n of |u_n| + c
  * (device arrays). */

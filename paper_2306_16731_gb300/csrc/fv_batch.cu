@@ -87,6 +87,13 @@ struct fv_batch {
     std::map<GraphKey, cudaGraphExec_t> graphs;
 
     int32_t *nbr = nullptr;            // device neighbour table (fv_batch_set_neighbours)
+
+    // host-state updates (fv_patch_batch_update_host): device staging and
+    // the copy streams, created by the first such call
+    void *hs_in = nullptr, *hs_out = nullptr;
+    double *hs_arrays = nullptr;       // dx, dt, lambda, dt_next (T each)
+    cudaStream_t hs_copy_in = nullptr, hs_copy_out = nullptr;
+    std::vector<cudaEvent_t> hs_events;
 };
 
 namespace fv {
@@ -589,6 +596,12 @@ int fv_batch_destroy(fv_batch_t *b)
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     if (b->scratch) cudaFree(b->scratch);
     if (b->nbr) cudaFree(b->nbr);
+    if (b->hs_in) cudaFree(b->hs_in);
+    if (b->hs_out) cudaFree(b->hs_out);
+    if (b->hs_arrays) cudaFree(b->hs_arrays);
+    if (b->hs_copy_in) cudaStreamDestroy(b->hs_copy_in);
+    if (b->hs_copy_out) cudaStreamDestroy(b->hs_copy_out);
+    for (cudaEvent_t e : b->hs_events) cudaEventDestroy(e);
     if (b->meta) cudaFree(b->meta);
     delete b;
     return FV_OK;
@@ -623,6 +636,105 @@ int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len)
 }
 
 }  // extern "C"
+
+
+namespace {
+
+constexpr int kMaxHostChunks = 64;
+
+int host_staging(fv_batch *b)
+{
+    if (b->hs_in) return FV_OK;
+    const size_t bytes = (size_t)b->state_elems * elem_bytes(b->precision);
+    cudaError_t e = cudaMalloc(&b->hs_in, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->hs_out, bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->hs_arrays, 4 * (size_t)b->T * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->hs_copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->hs_copy_out, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i < 2 * kMaxHostChunks + 1; ++i) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->hs_events.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FV_ENOMEM, "host-update staging: %s", cudaGetErrorString(e));
+    }
+    return FV_OK;
+}
+
+}  // namespace
+
+extern "C" int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, void *Q_out_host,
+                                          const double *dx_host, const double *dt_host, double *lambda_host,
+                                          double *dt_next_host, double cfl, int chunks)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (b->T == 0) return FV_OK;
+    if (!Q_in_host || !Q_out_host || !dx_host || !dt_host) return fail(FV_EINVAL, "NULL host pointer");
+    if (dt_next_host && !(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
+    if (chunks < 1 || chunks > kMaxHostChunks) return fail(FV_EINVAL, "chunks must be in [1, %d]", kMaxHostChunks);
+    DeviceGuard dg(b->device);
+    int rc = host_staging(b);
+    if (rc) return rc;
+    const size_t es = elem_bytes(b->precision);
+    double *d_dx = b->hs_arrays, *d_dt = d_dx + b->T, *d_lam = d_dt + b->T, *d_dtn = d_lam + b->T;
+    unsigned char *qi = static_cast<unsigned char *>(b->hs_in), *qo = static_cast<unsigned char *>(b->hs_out);
+    const unsigned char *hi = static_cast<const unsigned char *>(Q_in_host);
+    unsigned char *ho = static_cast<unsigned char *>(Q_out_host);
+
+    // Chunks are ranges of work items of a uniform fused batch (so each
+    // chunk's update is one launch over its own patches); any other batch
+    // runs as a single chunk.
+    const bool split = b->form == FV_FORM_FUSED && b->view.uniform_p > 0 && b->plan.num_classes == 1 &&
+                       !b->view.nbr && chunks > 1;
+    const int C = split ? std::min(chunks, b->plan.num_items) : 1;
+    const int per_item = split ? (b->plan.kernel == fv::FUSED_SWEEP2D ? 32 / b->view.uniform_p : 1) : b->T;
+    cudaEvent_t start = b->hs_events[2 * kMaxHostChunks];
+    cudaError_t e = cudaEventRecord(start, b->stream);      // order after earlier work on the batch stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hs_copy_in, start, 0);
+    for (int c = 0; c < C && e == cudaSuccess; ++c) {
+        const int item_lo = split ? (int)((int64_t)b->plan.num_items * c / C) : 0;
+        const int item_hi = split ? (int)((int64_t)b->plan.num_items * (c + 1) / C) : 0;
+        const int p_lo = split ? std::min(b->T, item_lo * per_item) : 0;
+        const int p_hi = split ? std::min(b->T, item_hi * per_item) : b->T;
+        const size_t o = (size_t)b->elem_off[p_lo] * es, n = (size_t)(b->elem_off[p_hi] - b->elem_off[p_lo]) * es;
+        const size_t a = (size_t)p_lo * sizeof(double), an = (size_t)(p_hi - p_lo) * sizeof(double);
+        cudaEvent_t ev_in = b->hs_events[2 * c], ev_done = b->hs_events[2 * c + 1];
+        e = cudaMemcpyAsync(qi + o, hi + o, n, cudaMemcpyHostToDevice, b->hs_copy_in);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((unsigned char *)d_dx + a, (const unsigned char *)dx_host + a, an,
+                                                  cudaMemcpyHostToDevice, b->hs_copy_in);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((unsigned char *)d_dt + a, (const unsigned char *)dt_host + a, an,
+                                                  cudaMemcpyHostToDevice, b->hs_copy_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in, b->hs_copy_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev_in, 0);
+        if (e != cudaSuccess) break;
+        fv::StepArgs args{qi, qo, d_dx, d_dt, lambda_host ? d_lam : nullptr, dt_next_host ? d_dtn : nullptr, cfl};
+        if (split) {
+            fv::FusedPlan sub = b->plan;
+            sub.num_classes = 1;
+            sub.class_begin[0] = item_lo;
+            sub.class_end[0] = item_hi;
+            e = fv::launch_fused_update(b->view, b->precision, args, sub, b->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "host update launch");
+        } else {
+            rc = launch_update(b, b->stream, qi, qo, d_dx, d_dt, args.lambda_out, args.dt_next_out, cfl);
+            if (rc) return rc;
+        }
+        e = cudaEventRecord(ev_done, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hs_copy_out, ev_done, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ho + o, qo + o, n, cudaMemcpyDeviceToHost, b->hs_copy_out);
+        if (e == cudaSuccess && lambda_host)
+            e = cudaMemcpyAsync((unsigned char *)lambda_host + a, (const unsigned char *)d_lam + a, an,
+                                cudaMemcpyDeviceToHost, b->hs_copy_out);
+        if (e == cudaSuccess && dt_next_host)
+            e = cudaMemcpyAsync((unsigned char *)dt_next_host + a, (const unsigned char *)d_dtn + a, an,
+                                cudaMemcpyDeviceToHost, b->hs_copy_out);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->hs_copy_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "host update");
+}
 
 // --------------------------------------------------------------- autotuner
 

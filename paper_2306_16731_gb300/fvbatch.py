@@ -38,7 +38,7 @@ _ERRNAMES = {FV_EINVAL: "FV_EINVAL", FV_ENOMEM: "FV_ENOMEM", FV_ECUDA: "FV_ECUDA
              FV_EUNSUPPORTED: "FV_EUNSUPPORTED", FV_ENONPHYSICAL: "FV_ENONPHYSICAL"}
 
 EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_batch_set_launch_shape",
-           "fv_batch_set_neighbours", "fv_halo_exchange",
+           "fv_batch_set_neighbours", "fv_halo_exchange", "fv_patch_batch_update_host",
            "fv_patch_batch_update", "fv_max_eigenvalue", "fv_cfl_time_step",
            "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
@@ -80,6 +80,7 @@ def load() -> ctypes.CDLL:
             "fv_batch_set_stream": (i, [_vp, _vp]),
             "fv_batch_set_launch_shape": (i, [_vp, i, i]),
             "fv_batch_set_neighbours": (i, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+            "fv_patch_batch_update_host": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, d, i]),
             "fv_halo_exchange": (i, [_vp, _vp]),
             "fv_patch_batch_update": (i, [_vp, _vp, _vp, _dp, _dp, _dp, _dp, d]),
             "fv_max_eigenvalue": (i, [_vp, _vp, _dp]),
@@ -166,6 +167,15 @@ def fv_batch_set_stream(b, stream):
 def fv_patch_batch_update(b, Q_in, Q_out, dx, dt, lambda_out=None, dt_next_out=None, cfl=0.4):
     return _check(load().fv_patch_batch_update(b, _addr(Q_in), _addr(Q_out), _addr(dx), _addr(dt),
                                                _addr(lambda_out), _addr(dt_next_out), float(cfl)))
+
+
+def fv_patch_batch_update_host(b, Q_in_host, Q_out_host, dx_host, dt_host, lambda_host=None,
+                               dt_next_host=None, cfl=0.4, chunks=8):
+    """Update with the state in host memory (pinned torch CPU tensors or
+    addresses); copies and updates pipelined over ``chunks`` patch ranges."""
+    return _check(load().fv_patch_batch_update_host(b, _addr(Q_in_host), _addr(Q_out_host), _addr(dx_host),
+                                                    _addr(dt_host), _addr(lambda_host), _addr(dt_next_host),
+                                                    float(cfl), int(chunks)))
 
 
 def fv_max_eigenvalue(b, Q, lambda_out):
@@ -262,6 +272,11 @@ class FVBatch:
 
     def update(self, Q_in, Q_out, dx, dt, lambda_out=None, dt_next_out=None, cfl=0.4):
         fv_patch_batch_update(self.handle, Q_in, Q_out, dx, dt, lambda_out, dt_next_out, cfl)
+
+    def update_host(self, Q_in_host, Q_out_host, dx_host, dt_host, lambda_host=None, dt_next_host=None,
+                    cfl=0.4, chunks=8):
+        fv_patch_batch_update_host(self.handle, Q_in_host, Q_out_host, dx_host, dt_host, lambda_host,
+                                   dt_next_host, cfl, chunks)
 
     def max_eigenvalue(self, Q, lambda_out):
         fv_max_eigenvalue(self.handle, Q, lambda_out)

@@ -481,3 +481,36 @@ def test_neighbour_table_is_validated():
     b.set_neighbours([[1, -1, -1, -1], [-1, 0, -1, -1], [-1] * 4])
     b.set_neighbours(None)
     b.close()
+
+
+@pytest.mark.parametrize("dim,sizes,precision", [(2, [16] * 700, 1), (3, [8] * 90, 1), (2, [16] * 64, 0),
+                                                 (2, [8, 16, 4, 8, 32] * 7, 1)])
+def test_host_state_update_matches_device_update(dim, sizes, precision):
+    """fv_patch_batch_update_host (pipelined chunks of host-to-device copy,
+    update, device-to-host copy) gives the device update's interiors,
+    eigenvalues and time steps bitwise, for any chunk count."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(dim, sizes, seed=130 + dim, dx=0.02)
+    T = w.num_patches
+    dtype = torch.float64 if precision == 0 else torch.float32
+    b = fb.FVBatch(dim, w.patch_size, precision=precision)
+    qa = torch.from_numpy(w.Q0).to("cuda", dtype)
+    qb = qa.clone()
+    dx = torch.tensor(w.dx, device="cuda")
+    dt = torch.full((T,), 2e-3, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dtn = torch.zeros_like(lam)
+    b.update(qa, qb, dx, dt, lam, dtn, 0.4)
+    torch.cuda.synchronize()
+    ref = patches_interior(qb.cpu().numpy(), dim, w.patch_size)
+    hin = qa.cpu().pin_memory()
+    for chunks in (1, 4, 7):
+        hout = torch.zeros_like(hin).pin_memory()
+        hl = torch.zeros(T, dtype=torch.float64).pin_memory()
+        hd = torch.zeros(T, dtype=torch.float64).pin_memory()
+        b.update_host(hin, hout, dx.cpu().pin_memory(), dt.cpu().pin_memory(), hl, hd, 0.4, chunks)
+        got = patches_interior(hout.numpy(), dim, w.patch_size)
+        assert all(np.array_equal(g, r) for g, r in zip(got, ref)), chunks
+        assert np.array_equal(hl.numpy(), lam.cpu().numpy()) and np.array_equal(hd.numpy(), dtn.cpu().numpy())
+    b.close()

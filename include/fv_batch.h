@@ -167,12 +167,17 @@ int fv_patch_batch_update(fv_batch_t *b, const void *Q_in, void *Q_out,
  * Sec. 4 "Data transfer").  Q_in_host / Q_out_host are host state buffers
  * (page-locked for full speed), dx_host / dt_host host arrays of
  * num_patches doubles, lambda_host / dt_next_host optional host outputs.
- * A uniform batch using the fused form is cut into `chunks` (1..64) ranges
- * of patches whose host-to-device copies, updates and device-to-host copies
+ * With chunks = 0 ("direct") the update kernels read Q_in_host and write
+ * Q_out_host through their device mappings (page-locked host memory is
+ * coherently addressable from the GPU on Grace-Blackwell); no staging is
+ * made, and unmapped buffers give FV_EINVAL.  With chunks in 1..64, a
+ * uniform batch using the fused form is cut into that many ranges of
+ * patches whose host-to-device copies, updates and device-to-host copies
  * run on three streams, so copies in both directions overlap each other and
- * the updates; any other batch runs as one chunk.  The first call creates
- * the device staging (two state buffers and four arrays of num_patches
- * doubles) and two copy streams, kept until fv_batch_destroy (FV_ENOMEM).
+ * the updates; any other batch runs as one chunk.  The first such call
+ * creates the device staging (two state buffers and four arrays of
+ * num_patches doubles) and two copy streams, kept until fv_batch_destroy
+ * (FV_ENOMEM).
  * Synchronous: returns when Q_out_host and the outputs are complete.  The
  * halo volumes of Q_out_host are unspecified.
  */

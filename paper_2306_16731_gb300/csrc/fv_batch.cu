@@ -673,8 +673,32 @@ extern "C" int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, 
     if (b->T == 0) return FV_OK;
     if (!Q_in_host || !Q_out_host || !dx_host || !dt_host) return fail(FV_EINVAL, "NULL host pointer");
     if (dt_next_host && !(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
-    if (chunks < 1 || chunks > kMaxHostChunks) return fail(FV_EINVAL, "chunks must be in [1, %d]", kMaxHostChunks);
+    if (chunks < 0 || chunks > kMaxHostChunks) return fail(FV_EINVAL, "chunks must be in [0, %d]", kMaxHostChunks);
     DeviceGuard dg(b->device);
+    if (chunks == 0) {
+        // direct: the kernels read and write the page-locked host buffers
+        // through their device mappings (coherent host memory), no staging
+        void *dqi = nullptr, *dqo = nullptr, *ddx = nullptr, *ddt = nullptr, *dl = nullptr, *dn = nullptr;
+        cudaError_t e = cudaHostGetDevicePointer(&dqi, const_cast<void *>(Q_in_host), 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dqo, Q_out_host, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&ddx, const_cast<double *>(dx_host), 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&ddt, const_cast<double *>(dt_host), 0);
+        if (e == cudaSuccess && lambda_host) e = cudaHostGetDevicePointer(&dl, lambda_host, 0);
+        if (e == cudaSuccess && dt_next_host) e = cudaHostGetDevicePointer(&dn, dt_next_host, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FV_EINVAL, "direct host update needs page-locked, mapped host buffers: %s",
+                        cudaGetErrorString(e));
+        }
+        int rc = check_update_args(b, dqi, dqo, static_cast<double *>(ddx), static_cast<double *>(ddt),
+                                   static_cast<double *>(dn), cfl);
+        if (rc) return rc;
+        rc = launch_update(b, b->stream, dqi, dqo, static_cast<double *>(ddx), static_cast<double *>(ddt),
+                           static_cast<double *>(dl), static_cast<double *>(dn), cfl);
+        if (rc) return rc;
+        e = cudaStreamSynchronize(b->stream);
+        return e == cudaSuccess ? FV_OK : cuda_fail(e, "direct host update");
+    }
     int rc = host_staging(b);
     if (rc) return rc;
     const size_t es = elem_bytes(b->precision);

@@ -487,7 +487,8 @@ def test_neighbour_table_is_validated():
                                                  (2, [8, 16, 4, 8, 32] * 7, 1)])
 def test_host_state_update_matches_device_update(dim, sizes, precision):
     """fv_patch_batch_update_host (pipelined chunks of host-to-device copy,
-    update, device-to-host copy) gives the device update's interiors,
+    update, device-to-host copy, or with 0 chunks the kernels working on the
+    mapped host buffers directly) gives the device update's interiors,
     eigenvalues and time steps bitwise, for any chunk count."""
     import torch
     from paper_2306_16731_gb300 import fvbatch as fb
@@ -505,7 +506,7 @@ def test_host_state_update_matches_device_update(dim, sizes, precision):
     torch.cuda.synchronize()
     ref = patches_interior(qb.cpu().numpy(), dim, w.patch_size)
     hin = qa.cpu().pin_memory()
-    for chunks in (1, 4, 7):
+    for chunks in (1, 4, 7, 0):
         hout = torch.zeros_like(hin).pin_memory()
         hl = torch.zeros(T, dtype=torch.float64).pin_memory()
         hd = torch.zeros(T, dtype=torch.float64).pin_memory()

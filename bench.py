@@ -52,7 +52,7 @@ def parse_args():
                     help="skip the secondary 3D / uneven workload lines")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--profile", choices=["fused_f32", "fused_f64", "cascade_f64", "tile_f32",
-                                          "fused3d_f32", "fused3d16_f32"],
+                                          "fused3d_f32", "fused3d16_f32", "fused3dper_f32"],
                     default=None, help="no timing: run a few launches of one form for ncu")
     ap.add_argument("--patches", type=int, default=None,
                     help="with --profile: batch size (default 65536, state larger than L2)")
@@ -661,14 +661,15 @@ def run_profile(args):
     if form_name.startswith("fused3d"):
         p3 = 16 if form_name == "fused3d16" else 8
         T = args.patches or (4096 if p3 == 16 else 16384)
-        w = inputs.uniform_batch(3, [p3] * T, seed=3, dx=0.01, dtype=np.float32)
+        halo = inputs.PERIODIC if form_name == "fused3dper" else inputs.FIXED
+        w = inputs.uniform_batch(3, [p3] * T, seed=3, dx=0.01, dtype=np.float32, halo_mode=halo)
         form_name = "fused"
     else:
         T = args.patches or 65536
         w = inputs.uniform_batch(2, [16] * T, seed=2, dx=0.01, dtype=np.float32)
     prec = {"f32": fb.FV_F32, "f64": fb.FV_F64}[prec_name]
     form = {"fused": fb.FV_FORM_FUSED, "cascade": fb.FV_FORM_CASCADE, "tile": fb.FV_FORM_TILE}[form_name]
-    b = fb.FVBatch(w.dim, w.patch_size, precision=prec, form=form)
+    b = fb.FVBatch(w.dim, w.patch_size, precision=prec, form=form, halo_mode=w.halo_mode)
     dtype = torch.float32 if prec == fb.FV_F32 else torch.float64
     qa = torch.from_numpy(w.Q0).to("cuda", dtype)
     qb = qa.clone()

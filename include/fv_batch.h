@@ -62,7 +62,9 @@ enum {
     FV_ENOMEM = -2,         /* host or device allocation failed */
     FV_ECUDA = -3,          /* a CUDA runtime call failed */
     FV_EUNSUPPORTED = -4,   /* valid request no kernel of this build covers */
-    FV_ENONPHYSICAL = -5    /* device met rho <= 0, p <= 0 or a non-finite eigenvalue */
+    FV_ENONPHYSICAL = -5,   /* device met rho <= 0, p <= 0 or a non-finite eigenvalue */
+    FV_ETIMEOUT = -6        /* a kernel's bounded wait for its own copy ran out (1 s); that
+                               update's results are invalid, the context stays usable */
 };
 
 /* Storage / compute precision of the state. */
@@ -79,7 +81,9 @@ enum {
     FV_HALO_FIXED = 0,      /* halo volumes are read from Q_in as given; each halo volume of Q_out is
                                either left as it is or set to Q_in's value (the fused 2D kernels write
                                the x-halo volumes of interior rows so that rows are written whole) */
-    FV_HALO_PERIODIC = 1    /* halo volumes are the wrapped interior of the same patch; halo memory is never read or written */
+    FV_HALO_PERIODIC = 1    /* halo volumes are the wrapped interior of the same patch; halo memory of Q_in is
+                               never read; halo volumes of Q_out are left untouched or set to the wrapped
+                               new values (fused kernels write rows whole, x-halo volumes included) */
 };
 
 /* Kernel realisation (Sec. 3). */
@@ -226,8 +230,9 @@ int fv_batch_run(fv_batch_t *b, void *Q_a, void *Q_b, const double *dx,
 int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out,
                   const double *dx, const double *dt);
 
-/* Synchronise the batch's stream and report FV_ENONPHYSICAL if any call
- * since the last status check met a non-physical state (and clear it). */
+/* Synchronise the batch's stream and report FV_ETIMEOUT if any kernel
+ * since the last status check gave up a bounded wait, else FV_ENONPHYSICAL
+ * if one met a non-physical state (and clear both). */
 int fv_batch_status(fv_batch_t *b);
 
 /* Free the batch (NULL-safe).  Synchronises its stream first. */

@@ -582,6 +582,8 @@ int fv_batch_status(fv_batch_t *b)
         unsigned zero = 0;
         e = cudaMemcpy(b->view.flags, &zero, sizeof zero, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "clear status flags");
+        if (flags & fv::FV_FLAG_TIMEOUT)
+            return fail(FV_ETIMEOUT, "a bounded device wait for a copy ran out; the update's results are invalid");
         return fail(FV_ENONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite eigenvalue) met on the device");
     }
     return FV_OK;
@@ -627,7 +629,8 @@ int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len)
     const char *form = b->form == FV_FORM_CASCADE ? "cascade" : (b->form == FV_FORM_TILE ? "tile" : "fused");
     const char *prec = b->precision == FV_F64 ? "f64" : (b->precision == FV_F32 ? "f32" : "bf16/f32");
     const char *fk = b->fused_kernel == fv::FUSED_SWEEP2D ? "sweep2d"
-                     : (b->fused_kernel == fv::FUSED_SWEEP3D ? "sweep3d" : "none");
+                     : (b->fused_kernel == fv::FUSED_SWEEP3D ? fv::fused3d_kernel_name(b->view, b->precision)
+                                                             : "none");
     snprintf(buf, len, "form=%s precision=%s dim=%d patches=%d max_p=%d uniform_p=%d fused_kernel=%s "
              "items=%d warps_per_block=%d blocks_per_sm=%d scratch_bytes=%zu",
              form, prec, b->dim, b->T, b->view.max_p, b->view.uniform_p, fk, b->plan.num_items,

@@ -93,6 +93,12 @@ bool fused_supported(const BatchView &b, int precision, int *kernel);
 bool fused3d_supported(const BatchView &b, int precision);
 cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepArgs &a,
                                   const FusedPlan &plan, cudaStream_t st);
+// name of the fused 3D kernel an update of this batch runs
+const char *fused3d_kernel_name(const BatchView &b, int precision);
+// periodic 8^3 patches, one warp per patch (fv_sweep3d_p8.cu)
+bool fused3d_p8_applies(const BatchView &b, int precision, const void *q_in, const void *q_out);
+cudaError_t launch_fused3d_p8(const BatchView &b, int precision, const StepArgs &a, int first, int count,
+                              const FusedShape &shape, cudaStream_t st);
 int fused_items_for(int dim, int p, int *patches_per_item);
 
 cudaError_t launch_halo_exchange(const BatchView &b, int precision, const int32_t *nbr, void *q,

@@ -211,8 +211,8 @@ __device__ __forceinline__ int wrap(int i, int p)
     return i < 0 ? i + p : (i >= p ? i - p : i);
 }
 
-// Error flag bits.
-enum : unsigned { FV_FLAG_NONPHYSICAL = 1u };
+// Error flag bits: a non-physical state; a bounded device wait that ran out.
+enum : unsigned { FV_FLAG_NONPHYSICAL = 1u, FV_FLAG_TIMEOUT = 2u };
 
 // Atomic maximum of a non-negative double via its bit pattern (ordered as
 // a signed 64-bit integer for non-negative values).

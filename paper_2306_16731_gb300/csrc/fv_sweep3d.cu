@@ -707,6 +707,14 @@ bool fused3d_supported(const BatchView &b, int precision)
     return general || blocks8;
 }
 
+const char *fused3d_kernel_name(const BatchView &b, int precision)
+{
+    if (b.dim != 3) return "none";
+    if (b.uniform_p == 8 && b.halo_mode == 1 && precision != PREC_F64) return "sweep3d_p8";
+    if (b.uniform_p > 0 && b.uniform_p % 8 == 0 && b.uniform_p <= 32 && precision != PREC_F64) return "sweep3d_b8";
+    return "sweep3d";
+}
+
 cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepArgs &a, const FusedPlan &plan,
                                   cudaStream_t st)
 {
@@ -724,6 +732,15 @@ cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepA
     sp.order = plan.order;
     // every patch base is a multiple of the smallest power-of-two alignment
     // of all patch sizes in bytes (the buffer itself is 16-byte aligned)
+    if (fused3d_p8_applies(b, precision, a.q_in, a.q_out)) {
+        // uniform batch: one size class (or the item range of a sub-plan)
+        for (int c = 0; c < plan.num_classes; ++c) {
+            cudaError_t e = launch_fused3d_p8(b, precision, a, plan.class_begin[c],
+                                              plan.class_end[c] - plan.class_begin[c], plan.shape, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const size_t es = precision == PREC_F64 ? 8 : (precision == PREC_F32 ? 4 : 2);
     int chunk = 16;
     for (int c = 0; c < plan.num_classes; ++c) {

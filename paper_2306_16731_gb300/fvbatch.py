@@ -22,6 +22,7 @@ FV_ENOMEM = -2
 FV_ECUDA = -3
 FV_EUNSUPPORTED = -4
 FV_ENONPHYSICAL = -5
+FV_ETIMEOUT = -6
 
 FV_F64 = 0
 FV_F32 = 1
@@ -35,7 +36,8 @@ FV_FORM_CASCADE = 1
 FV_FORM_TILE = 2
 
 _ERRNAMES = {FV_EINVAL: "FV_EINVAL", FV_ENOMEM: "FV_ENOMEM", FV_ECUDA: "FV_ECUDA",
-             FV_EUNSUPPORTED: "FV_EUNSUPPORTED", FV_ENONPHYSICAL: "FV_ENONPHYSICAL"}
+             FV_EUNSUPPORTED: "FV_EUNSUPPORTED", FV_ENONPHYSICAL: "FV_ENONPHYSICAL",
+             FV_ETIMEOUT: "FV_ETIMEOUT"}
 
 EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_batch_set_launch_shape",
            "fv_batch_set_neighbours", "fv_halo_exchange", "fv_patch_batch_update_host",

@@ -21,7 +21,7 @@ import pytest
 import oracle
 from paper_2306_16731_gb300 import inputs
 from tests._helpers import batch_rel_linf, batch_rel_linf_components, patches_interior
-from tests.gpu_util import gpu_run, initial_fp64, subset, take_patches, to_device
+from tests.gpu_util import gpu_run, initial_fp64, subset, take_patches, to_device, torch_dtype
 
 pytestmark = pytest.mark.gpu
 
@@ -515,3 +515,60 @@ def test_host_state_update_matches_device_update(dim, sizes, precision):
         assert all(np.array_equal(g, r) for g, r in zip(got, ref)), chunks
         assert np.array_equal(hl.numpy(), lam.cpu().numpy()) and np.array_equal(hd.numpy(), dtn.cpu().numpy())
     b.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("T", [1, 5, 37, 700])
+def test_periodic_8cubed_warp_kernel_shapes_and_oracle(precision, T):
+    """Periodic 8^3 patches run the one-warp-per-patch kernel (bulk-copied
+    plane ring, packed pair arithmetic).  Every launch shape gives the same
+    bits, including shapes where one warp walks several patches (its copy
+    ring then runs across patches); the state and eigenvalues match the
+    oracle's periodic step from the same (rounded) start."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(3, [8] * T, seed=90 + T, dx=np.linspace(0.05, 0.1, T),
+                             halo_mode=inputs.PERIODIC)
+    dtype = torch_dtype(precision)
+    results = []
+    for shape in [(4, 0), (1, 0), (3, 0), (16, -1), (1, 1), (2, 1), (8, 2)]:
+        b = fb.FVBatch(3, w.patch_size, precision=precision, halo_mode=inputs.PERIODIC)
+        b.set_launch_shape(*shape)
+        assert "fused_kernel=sweep3d_p8" in b.describe()
+        qa = to_device(w.Q0, precision)
+        qb = torch.zeros_like(qa)
+        dx = torch.tensor(w.dx, device="cuda")
+        dt = torch.full((T,), 2e-3, dtype=torch.float64, device="cuda")
+        lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+        dtn = torch.zeros_like(lam)
+        b.update(qa, qb, dx, dt, lam, dtn, 0.4)
+        b.status()
+        results.append((qb.to(torch.float64).cpu().numpy(), lam.cpu().numpy(), dtn.cpu().numpy()))
+        b.close()
+    for q, l, d in results[1:]:
+        assert np.array_equal(patches_interior(q, 3, w.patch_size), patches_interior(results[0][0], 3, w.patch_size))
+        assert np.array_equal(l, results[0][1]) and np.array_equal(d, results[0][2])
+    q0 = initial_fp64(w.Q0, precision)
+    ref, lam_ref = oracle.batch_step(3, w.patch_size, w.dx, [2e-3] * T, q0, halo_mode=inputs.PERIODIC)
+    tol = 1e-5 if precision == 1 else 2e-2
+    assert batch_rel_linf(results[0][0], ref, 3, w.patch_size) < tol
+    assert np.max(np.abs(results[0][1] - lam_ref) / lam_ref) < (1e-5 if precision == 1 else 2e-2)
+    assert np.allclose(results[0][2], 0.4 * np.asarray(w.dx) / (3 * results[0][1]), rtol=1e-15, atol=0)
+    # rows are written whole: x-halo volumes of interior rows hold the wrapped values
+    E = 10
+    qf = results[0][0].reshape(T, E, E, E, 5)
+    assert np.array_equal(qf[:, 1:-1, 1:-1, E - 1], qf[:, 1:-1, 1:-1, 1])
+    assert np.array_equal(qf[:, 1:-1, 1:-1, 0], qf[:, 1:-1, 1:-1, E - 2])
+
+
+def test_periodic_8cubed_warp_kernel_agrees_with_tile_form():
+    w = inputs.uniform_batch(3, [8] * 200, seed=97, halo_mode=inputs.PERIODIC, dtype=np.float32)
+    fused = gpu_run(w, 1, FORMS["fused"], 8)
+    tile = gpu_run(w, 1, FORMS["tile"], 8)
+    assert "sweep3d_p8" in fused[3]
+    ref, _, _ = oracle.batch_run(3, w.patch_size, w.dx, initial_fp64(w.Q0, 1), 8, halo_mode=inputs.PERIODIC)
+    e_f = batch_rel_linf(fused[0], ref, 3, w.patch_size)
+    e_t = batch_rel_linf(tile[0], ref, 3, w.patch_size)
+    print("periodic 8^3 FP32 after 8 steps: warp kernel %.2e, tile form %.2e" % (e_f, e_t))
+    assert e_f < 1e-5 and e_t < 1e-5
+    assert batch_rel_linf(fused[0], tile[0], 3, w.patch_size) < 1e-5

@@ -223,7 +223,9 @@ int fv_batch_run(fv_batch_t *b, void *Q_a, void *Q_b, const double *dx,
  * Autotune the fused form: time every candidate launch shape of this
  * batch's kernel on the given buffers (contents of Q_out are overwritten),
  * check that every candidate's output is bitwise identical to the first
- * one's, and keep the fastest.  Results are cached per device and batch
+ * one's, and keep the fastest.  Each timed launch follows a read of a
+ * scratch buffer twice the size of L2 (allocated for the call, FV_ENOMEM if
+ * it cannot be), so candidates are timed with their input in HBM.  Results are cached per device and batch
  * shape in memory and, if the environment variable FVBATCH_TUNE_CACHE names
  * a file, in that file.  Synchronises the stream.
  */

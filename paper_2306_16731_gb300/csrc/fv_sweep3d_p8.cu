@@ -375,8 +375,22 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
                 S *ra = reinterpret_cast<S *>(stg + sa + (2 * j) * G::row);
                 S *rb = reinterpret_cast<S *>(stg + sa + (2 * j + 1) * G::row);
                 store_pair<S>(ra + (x + 1) * kN, rb + (x + 1) * kN, qn);
-                if (x == 0) store_pair<S>(ra + (kP + 1) * kN, rb + (kP + 1) * kN, qn);    // +x halo
-                if (x == kP - 1) store_pair<S>(ra, rb, qn);                                // -x halo
+                __syncwarp();
+                // x-halo volumes: lane r < 8 copies column 8 of row r to the
+                // -x halo (column 0), lane 8 + r column 1 to the +x halo
+                // (column 9); the 16 source words of each unknown fall in
+                // distinct banks
+                if (lane < 16) {
+                    const int r = lane & 7, up = lane >> 3;
+                    S *row = reinterpret_cast<S *>(stg + sa + r * G::row);
+                    const S *src = row + (up ? 1 : kP) * kN;
+                    S *dst = row + (up ? kP + 1 : 0) * kN;
+                    S v[kN];
+#pragma unroll
+                    for (int k = 0; k < kN; ++k) v[k] = src[k];
+#pragma unroll
+                    for (int k = 0; k < kN; ++k) dst[k] = v[k];
+                }
                 fence_proxy_async_smem();
                 __syncwarp();
                 unsigned char *gbase = sp.q_out + patch * G::patch + (G::rows_begin(zf) - sa);   // 16-aligned

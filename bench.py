@@ -129,9 +129,10 @@ def _oracle_sample(w, idx):
     return np.concatenate([np.asarray(w.Q0[off[i]:off[i + 1]], dtype=np.float64) for i in idx])
 
 
-def cpu_baseline(w, seconds, sample_patches=1024, steps=1):
+def cpu_baseline(w, seconds, sample_patches=1024, steps=1, threads=0):
     import oracle
     oracle.build()
+    oracle.set_num_threads(threads)
     rng = np.random.default_rng(12345)
     idx = np.sort(rng.choice(w.num_patches, min(sample_patches, w.num_patches), replace=False))
     Q = _oracle_sample(w, idx)
@@ -150,7 +151,9 @@ def cpu_baseline(w, seconds, sample_patches=1024, steps=1):
     value = vols * steps * runs / el
     desc = ("%d seeded patches of the workload x %d step(s), repeated %d times (%.1f s)"
             % (len(idx), steps, runs, el))
-    return value, oracle.num_threads(), desc
+    cores = oracle.num_threads()
+    oracle.set_num_threads(0)
+    return value, cores, desc
 
 
 def oracle_error(w, Q0_f32, gpu_final, steps, idx):
@@ -419,12 +422,15 @@ def run_ours(args):
         out["workloads"] = forms_other
     if "cascade_f64" in forms:
         out["speedup_fused_f32_vs_cascade_f64"] = forms["fused_f32"]["value"] / forms["cascade_f64"]["value"]
+    # the paper's unit: time per degree-of-freedom update (volume updates x N unknowns)
+    out["cost_per_dof_update_ns"] = (ms_max / args.steps) * 1e6 / (vols * N)
 
     if not args.no_cpu_baseline and world == 1:
         wd = inputs.config(2, dtype=np.float64)
         v, cores, desc = cpu_baseline(wd, args.cpu_seconds)
+        v1, _, desc1 = cpu_baseline(wd, max(1.0, args.cpu_seconds / 2), sample_patches=128, threads=1)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": desc}
+                               "sample": desc, "single_thread": {"value": v1, "cores": 1, "sample": desc1}}
         idx = np.sort(np.random.default_rng(7).choice(T, 16, replace=False))
         err, comps, _ = oracle_error(wd, None, final, w.steps, idx)
         out["error_vs_oracle"] = {"rel_linf": err, "rel_linf_per_unknown": comps,

@@ -148,6 +148,15 @@ int fv_halo_exchange(fv_batch_t *b, void *Q);
 /* Rebind the batch to another stream (e.g. a capture stream). */
 int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream);
 
+/* Test hook for the timeout path; the paper has no counterpart.  With
+ * enable != 0, updates that run the periodic 8^3 kernel make each warp's
+ * first plane wait expect 16 bytes more than its copy delivers, so the
+ * bounded wait runs out after 1 s: the warp drains its copies, writes
+ * nothing more and the next fv_batch_status reports FV_ETIMEOUT.  Nothing
+ * faults; the context stays usable.  enable = 0 restores normal updates.
+ * Other kernels ignore it. */
+int fv_batch_test_wait_expiry(fv_batch_t *b, int enable);
+
 /*
  * One explicit time step (Sec. 2.2, Eq. 2, Algorithm 1):
  *   Q_out = Q_in - dt_i/dx_i * sum_n (Fhat_n(c+1/2) - Fhat_n(c-1/2))

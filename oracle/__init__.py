@@ -15,6 +15,7 @@ from .fv_oracle import (  # noqa: F401
     batch_totals,
     halo_exchange,
     num_threads,
+    set_num_threads,
     FIXED,
     PERIODIC,
 )

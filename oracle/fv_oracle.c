@@ -405,6 +405,17 @@ int fvo_num_threads(void)
 #endif
 }
 
+/* Threads for the following batch loops (timing the oracle on one core or
+ * on all of them); n < 1 restores the OpenMP default. */
+void fvo_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
 /* Halo fill from neighbouring patches (the step before the kernel call in
  * the paper's framework: patches are equipped with a halo layer of width one
  * taken from their neighbours, Sec. 2.2).  nbr has 2*dim entries per patch in

@@ -76,6 +76,8 @@ def bind(path: str):
     lib.fvo_halo_exchange.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp]
     lib.fvo_num_threads.restype = ctypes.c_int
     lib.fvo_num_threads.argtypes = []
+    lib.fvo_set_num_threads.restype = None
+    lib.fvo_set_num_threads.argtypes = [ctypes.c_int]
     return lib
 
 
@@ -222,3 +224,8 @@ def halo_exchange(dim, patch_size, neighbours, Q):
 def num_threads() -> int:
     """Threads the oracle's batch loops run on."""
     return int(_load().fvo_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Run the following batch loops on n threads (n < 1: the default)."""
+    _load().fvo_set_num_threads(int(n))

@@ -436,6 +436,14 @@ int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per
     return FV_OK;
 }
 
+int fv_batch_test_wait_expiry(fv_batch_t *b, int enable)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    b->view.test_wait_expiry = enable ? 1 : 0;
+    drop_graphs(b);
+    return FV_OK;
+}
+
 int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream)
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");

@@ -25,6 +25,7 @@ struct BatchView {
     int uniform_p;             // p if all patches share it, else 0
     int align_bytes;           // largest power of two <= 16 dividing every patch's (and 3D plane's) bytes
     const int32_t *nbr;        // [T][2 dim] neighbour across -x,+x,-y,+y[,-z,+z] or -1; null = none registered
+    int test_wait_expiry;      // test hook: bounded copy waits are made to run out (FV_ETIMEOUT)
 };
 
 // Arguments of one update.

@@ -68,6 +68,7 @@ struct P8Params {
     unsigned *flags;
     int first;                    // first patch of the launch
     int count;                    // patches
+    unsigned extra_tx;            // test hook: bytes the first plane wait expects beyond its copy
 };
 
 // ------------------------------------------------------- packed arithmetic
@@ -198,13 +199,14 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Wait for the phase of `bar` with the given parity, at most kWaitLimitNs.
+// Wait for the phase of `bar` with the given parity, at most kWaitLimitNs
+// (and at most 2^24 polls, should the global timer not advance).
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (!mbar_try(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+    for (unsigned polls = 0; !mbar_try(bar, parity); ++polls)
+        if (global_ns() - t0 > kWaitLimitNs || polls >= (1u << 24)) return false;
     return true;
 }
 
@@ -289,19 +291,19 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
     // ((s / 5) mod 2) are the same for every patch, so after unrolling the
     // steps they are constants.  The load of step s + 4 is issued at step s
     // (for s + 4 >= 10: step s - 6 of the warp's next patch).
-    auto issue = [&](int64_t patch, int zz, int slot) {
+    auto issue = [&](int64_t patch, int zz, int slot, unsigned extra) {
         if (lane != 0) return;
         const int rb = G::rows_begin(zz);
         const int lo = rb & ~15, hi = (rb + 8 * G::row + 15) & ~15;
         // the slot's previous plane was loaded into registers and used by
         // every lane before the __syncwarp that precedes this call
-        mbar_expect_tx(bar0 + 8u * slot, (unsigned)(hi - lo));
+        mbar_expect_tx(bar0 + 8u * slot, (unsigned)(hi - lo) + extra);
         bulk_g2s(slot0 + (unsigned)(slot * G::slot), sp.q_in + patch * G::patch + lo, (unsigned)(hi - lo),
                  bar0 + 8u * slot);
     };
     const int64_t patch0 = sp.first + gw;
 #pragma unroll
-    for (int s = 0; s < kSlots - 1; ++s) issue(patch0, (s + kP - 1) & (kP - 1), s);
+    for (int s = 0; s < kSlots - 1; ++s) issue(patch0, (s + kP - 1) & (kP - 1), s, s == 0 ? sp.extra_tx : 0u);
 
     const int x = lane & 7, j = lane >> 3;
     const int src_r = (lane & 24) | ((x + 1) & 7), src_l = (lane & 24) | ((x + 7) & 7);
@@ -328,8 +330,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
             __syncwarp();                               // slot of step s-1 consumed by all lanes
             {
                 const int sn = s + kSlots - 1;
-                if (sn < kStepsPerPatch) issue(patch, (sn + kP - 1) & (kP - 1), sn % kSlots);
-                else if (has_next) issue(patch + nwarps, (sn - kStepsPerPatch + kP - 1) & (kP - 1), sn % kSlots);
+                if (sn < kStepsPerPatch) issue(patch, (sn + kP - 1) & (kP - 1), sn % kSlots, 0u);
+                else if (has_next) issue(patch + nwarps, (sn - kStepsPerPatch + kP - 1) & (kP - 1), sn % kSlots, 0u);
             }
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar0 + 8u * (s % kSlots), (s / kSlots) & 1))) {
                 waited = pi * kStepsPerPatch + s;
@@ -484,7 +486,7 @@ timeout:
         const int total = mine * kStepsPerPatch;
         const int issued = total < waited + kSlots ? total : waited + kSlots;
         for (int t = waited; t < issued; ++t)
-            if (!mbar_wait_bounded(bar0 + 8u * (unsigned)(t % kSlots), (unsigned)(t / kSlots) & 1u)) break;
+            mbar_wait_bounded(bar0 + 8u * (unsigned)(t % kSlots), (unsigned)(t / kSlots) & 1u);
     }
     if (lane == 0) atomicOr(sp.flags, FV_FLAG_TIMEOUT);
 }
@@ -555,6 +557,7 @@ cudaError_t launch_fused3d_p8(const BatchView &b, int precision, const StepArgs 
     sp.flags = b.flags;
     sp.first = first;
     sp.count = count;
+    sp.extra_tx = b.test_wait_expiry ? 16u : 0u;
     if (precision == PREC_F32) return launch_p8<float>(sp, precision, shape, st);
     return launch_p8<__nv_bfloat16>(sp, precision, shape, st);
 }

@@ -44,7 +44,8 @@ EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_ba
            "fv_patch_batch_update", "fv_max_eigenvalue", "fv_cfl_time_step",
            "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
-           "fv_batch_scratch_bytes", "fv_batch_describe", "fv_batch_launches_per_update"]
+           "fv_batch_scratch_bytes", "fv_batch_describe", "fv_batch_launches_per_update",
+           "fv_batch_test_wait_expiry"]
 
 
 class FVError(RuntimeError):
@@ -81,6 +82,7 @@ def load() -> ctypes.CDLL:
             "fv_batch_set_form": (i, [_vp, i]),
             "fv_batch_set_stream": (i, [_vp, _vp]),
             "fv_batch_set_launch_shape": (i, [_vp, i, i]),
+            "fv_batch_test_wait_expiry": (i, [_vp, i]),
             "fv_batch_set_neighbours": (i, [_vp, ctypes.POINTER(ctypes.c_int32)]),
             "fv_patch_batch_update_host": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, d, i]),
             "fv_halo_exchange": (i, [_vp, _vp]),
@@ -160,6 +162,10 @@ def fv_halo_exchange(b, Q):
 
 def fv_batch_set_launch_shape(b, warps_per_block, blocks_per_sm):
     return _check(load().fv_batch_set_launch_shape(b, int(warps_per_block), int(blocks_per_sm)))
+
+
+def fv_batch_test_wait_expiry(b, enable):
+    return _check(load().fv_batch_test_wait_expiry(b, 1 if enable else 0))
 
 
 def fv_batch_set_stream(b, stream):
@@ -268,6 +274,10 @@ class FVBatch:
 
     def set_launch_shape(self, warps_per_block, blocks_per_sm):
         fv_batch_set_launch_shape(self.handle, warps_per_block, blocks_per_sm)
+
+    def test_wait_expiry(self, enable):
+        """Test hook: make the bounded copy waits of the periodic 8^3 kernel run out."""
+        fv_batch_test_wait_expiry(self.handle, enable)
 
     def set_stream(self, stream):
         fv_batch_set_stream(self.handle, stream)

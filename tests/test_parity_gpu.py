@@ -572,3 +572,37 @@ def test_periodic_8cubed_warp_kernel_agrees_with_tile_form():
     print("periodic 8^3 FP32 after 8 steps: warp kernel %.2e, tile form %.2e" % (e_f, e_t))
     assert e_f < 1e-5 and e_t < 1e-5
     assert batch_rel_linf(fused[0], tile[0], 3, w.patch_size) < 1e-5
+
+
+def test_bounded_copy_wait_reports_timeout_and_context_survives():
+    """A plane wait that can never complete (the test hook makes it expect 16
+    bytes more than its copy delivers) gives up after its 1 s bound: the
+    update reports FV_ETIMEOUT, nothing faults, and the next normal update
+    on the same context matches the oracle."""
+    import time
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    T = 6
+    w = inputs.uniform_batch(3, [8] * T, seed=99, halo_mode=inputs.PERIODIC, dtype=np.float32)
+    b = fb.FVBatch(3, w.patch_size, precision=1, halo_mode=inputs.PERIODIC)
+    assert "sweep3d_p8" in b.describe()
+    qa = to_device(w.Q0, 1)
+    qb = torch.zeros_like(qa)
+    dx = torch.tensor(w.dx, device="cuda")
+    dt = torch.full((T,), 1e-3, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    b.test_wait_expiry(True)
+    t0 = time.perf_counter()
+    b.update(qa, qb, dx, dt, lam, None, 0.4)
+    with pytest.raises(fb.FVError) as ei:
+        b.status()
+    elapsed = time.perf_counter() - t0
+    assert ei.value.code == fb.FV_ETIMEOUT
+    assert 0.9 < elapsed < 20.0
+    b.test_wait_expiry(False)
+    b.update(qa, qb, dx, dt, lam, None, 0.4)
+    b.status()
+    ref, lam_ref = oracle.batch_step(3, w.patch_size, w.dx, [1e-3] * T, initial_fp64(w.Q0, 1),
+                                     halo_mode=inputs.PERIODIC)
+    assert batch_rel_linf(qb.to(torch.float64).cpu().numpy(), ref, 3, w.patch_size) < 1e-5
+    b.close()

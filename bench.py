@@ -379,8 +379,10 @@ def run_ours(args):
 
     if not args.no_other_workloads and world == 1:
         forms_other = other_workloads(dev, stream, flush_l2, args.steps)
+        abl = ablations(dev, stream, flush_l2)
     else:
         forms_other = None
+        abl = None
     clk = clocks.stop()
 
     if rank != 0:
@@ -420,6 +422,8 @@ def run_ours(args):
            "forms": forms}
     if forms_other is not None:
         out["workloads"] = forms_other
+    if abl is not None:
+        out["ablations"] = abl
     if "cascade_f64" in forms:
         out["speedup_fused_f32_vs_cascade_f64"] = forms["fused_f32"]["value"] / forms["cascade_f64"]["value"]
     # the paper's unit: time per degree-of-freedom update (volume updates x N unknowns)
@@ -440,6 +444,71 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return out
+
+
+def ablations(dev, stream, flush_l2, k=5):
+    """The paper's realisation and layout comparisons on the 2D 16x16 FP64
+    workload: the batched loop cascade with AoS, SoA and AoSoA temporaries
+    (App. C), and the task-graph realisation (one graph node per patch, step
+    and axis, Sec. 3) against the cascade at growing batch sizes."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb, inputs
+    res = {}
+
+    def setup(w, form, layout=0):
+        b = fb.FVBatch(2, w.patch_size, precision=0, form=form, stream=stream.cuda_stream)
+        b.set_cascade_layout(layout)
+        qs = [torch.from_numpy(w.Q0).to(dev), None]
+        qs[1] = qs[0].clone()
+        dx = torch.tensor(w.dx, device=dev)
+        lam = torch.zeros(w.num_patches, dtype=torch.float64, device=dev)
+        dts = [torch.full((w.num_patches,), 1e-4, dtype=torch.float64, device=dev) for _ in range(2)]
+        return b, qs, dx, lam, dts
+
+    def steps(b, qs, dx, lam, dts):
+        t0 = time.perf_counter()
+        for s_ in range(2):                       # first use builds graphs (task-graph form)
+            b.update(qs[s_ & 1], qs[1 - (s_ & 1)], dx, dts[s_ & 1], lam, dts[1 - (s_ & 1)], 0.4)
+        torch.cuda.synchronize()
+        first = time.perf_counter() - t0
+        tot = 0.0
+        for s_ in range(k):
+            i = s_ & 1
+            flush_l2()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.update(qs[i], qs[1 - i], dx, dts[i], lam, dts[1 - i], 0.4)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        b.status()
+        return tot / k, first
+
+    w = inputs.config(2, dtype=np.float64)
+    lay = {}
+    for name, layout in (("aos", 0), ("soa", 1), ("aosoa", 2)):
+        b, qs, dx, lam, dts = setup(w, 1, layout)
+        ms, _ = steps(b, qs, dx, lam, dts)
+        lay[name] = {"value": w.interior_volumes / (ms / 1e3), "ms_per_step": ms}
+        b.close()
+        del qs
+    res["cascade_f64_temporaries_layout_2d_p16_T16384"] = lay
+    tg = {}
+    for T in (256, 2048, 16384):
+        wt = inputs.uniform_batch(2, [16] * T, seed=2, dx=0.01)
+        row = {}
+        for name, form in (("taskgraph", 3), ("cascade", 1), ("fused", 0)):
+            b, qs, dx, lam, dts = setup(wt, form)
+            ms, first = steps(b, qs, dx, lam, dts)
+            row[name] = {"value": wt.interior_volumes / (ms / 1e3), "ms_per_step": ms}
+            if form == 3:
+                row[name]["graph_kernel_nodes"] = b.launches_per_update()
+                row[name]["first_two_updates_s"] = first
+            b.close()
+            del qs
+        tg["T%d" % T] = row
+    res["taskgraph_vs_batched_f64_2d_p16"] = tg
+    return res
 
 
 def other_workloads(dev, stream, flush_l2, steps):

@@ -90,7 +90,12 @@ enum {
 enum {
     FV_FORM_FUSED = 0,      /* default: one fused launch per step (warp-level sweep kernels) */
     FV_FORM_CASCADE = 1,    /* one launch per algorithmic step over all volumes, intermediates in device memory (batched realisation) */
-    FV_FORM_TILE = 2        /* one thread block per patch staged in shared memory (patch-wise realisation) */
+    FV_FORM_TILE = 2,       /* one thread block per patch staged in shared memory (patch-wise realisation) */
+    FV_FORM_TASKGRAPH = 3   /* task-graph realisation (Sec. 3): one CUDA graph per update whose nodes are the
+                               cascade's kernels restricted to one patch (and one axis for fluxes and faces),
+                               linked only by data dependencies; axes and patches run concurrently; bitwise
+                               equal to FV_FORM_CASCADE; the graph is built and instantiated on the first
+                               update with a buffer set (cost grows with T) and cannot be stream-captured */
 };
 
 /*
@@ -112,6 +117,14 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches,
  * build has no kernel of that form for the batch's shapes; the previous
  * form stays selected.  May allocate the cascade's scratch (FV_ENOMEM). */
 int fv_batch_set_form(fv_batch_t *b, int form);
+
+/* Layout of the cascade's and the task graph's vector temporaries (the
+ * fluxes F_n and face fluxes; the paper's App. C): FV_LAYOUT_AOS (default,
+ * [axis][cell][unknown]), FV_LAYOUT_SOA ([axis][unknown][cell]) or
+ * FV_LAYOUT_AOSOA ([axis][cell/32][unknown][cell%32]).  Results are bitwise
+ * independent of the layout.  FV_EINVAL for another value. */
+enum { FV_LAYOUT_AOS = 0, FV_LAYOUT_SOA = 1, FV_LAYOUT_AOSOA = 2 };
+int fv_batch_set_cascade_layout(fv_batch_t *b, int layout);
 
 /* Launch shape of the fused form: warps_per_block in [1, 16]; blocks_per_sm
  * 0 = one warp per work item (grid covers the work list), > 0 = that many

@@ -68,6 +68,7 @@ struct fv_batch {
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
     int form = FV_FORM_FUSED;
+    int cascade_layout = FV_LAYOUT_AOS;
 
     std::vector<int32_t> psize;
     std::vector<int64_t> elem_off, cell_off, int_off;
@@ -358,7 +359,7 @@ int fv_batch_set_form(fv_batch_t *b, int form)
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
-    if (form == FV_FORM_CASCADE) {
+    if (form == FV_FORM_CASCADE || form == FV_FORM_TASKGRAPH) {
         int rc = ensure_scratch(b);
         if (rc) return rc;
     } else if (form == FV_FORM_TILE) {
@@ -436,6 +437,16 @@ int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per
     return FV_OK;
 }
 
+int fv_batch_set_cascade_layout(fv_batch_t *b, int layout)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (layout != FV_LAYOUT_AOS && layout != FV_LAYOUT_SOA && layout != FV_LAYOUT_AOSOA)
+        return fail(FV_EINVAL, "unknown cascade layout %d", layout);
+    if (b->cascade_layout != layout) drop_graphs(b);
+    b->cascade_layout = layout;
+    return FV_OK;
+}
+
 int fv_batch_test_wait_expiry(fv_batch_t *b, int enable)
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
@@ -451,6 +462,34 @@ int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream)
     return FV_OK;
 }
 
+// Task-graph form: build and instantiate the per-patch graph of this buffer
+// set on first use (cached with the batch's graphs), then launch it.
+static int launch_taskgraph(fv_batch_t *b, cudaStream_t st, const fv::StepArgs &a)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "capture query");
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(FV_EUNSUPPORTED, "the task-graph form is itself a graph and cannot be stream-captured");
+    GraphKey key{a.q_in, a.q_out, a.dx, a.dt, a.dt_next_out, a.lambda_out, -1, a.cfl, FV_FORM_TASKGRAPH};
+    auto it = b->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it != b->graphs.end()) {
+        exec = it->second;
+    } else {
+        cudaGraph_t graph = nullptr;
+        e = cudaGraphCreate(&graph, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "graph create");
+        e = fv::build_cascade_taskgraph(b->view, b->cell_off.data(), b->precision, a, b->cs, b->cascade_layout, graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "task graph build");
+        b->graphs[key] = exec;
+    }
+    e = cudaGraphLaunch(exec, st);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "task graph launch");
+}
+
 static int launch_update(fv_batch_t *b, cudaStream_t st, const void *Q_in, void *Q_out,
                          const double *dx, const double *dt, double *lambda_out,
                          double *dt_next_out, double cfl)
@@ -459,7 +498,10 @@ static int launch_update(fv_batch_t *b, cudaStream_t st, const void *Q_in, void 
     fv::StepArgs a{Q_in, Q_out, dx, dt, lambda_out, dt_next_out, cfl};
     cudaError_t e;
     switch (b->form) {
-    case FV_FORM_CASCADE: e = fv::launch_cascade_update(b->view, b->precision, a, b->cs, st); break;
+    case FV_FORM_CASCADE:
+        e = fv::launch_cascade_update(b->view, b->precision, a, b->cs, st, b->cascade_layout);
+        break;
+    case FV_FORM_TASKGRAPH: return launch_taskgraph(b, st, a);
     case FV_FORM_TILE: e = fv::launch_tile_update(b->view, b->precision, a, st); break;
     default: e = fv::launch_fused_update(b->view, b->precision, a, b->plan, st); break;
     }
@@ -550,7 +592,9 @@ int fv_batch_run(fv_batch_t *b, void *Q_a, void *Q_b, const double *dx, double *
     if (b->T > 0 && !dt_b) return fail(FV_EINVAL, "dt_b is NULL");
     if (steps == 0 || b->T == 0) return FV_OK;
     DeviceGuard dg(b->device);
-    if (!use_graph) return enqueue_steps(b, b->stream, Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl);
+    // the task-graph form launches one graph per step already
+    if (!use_graph || b->form == FV_FORM_TASKGRAPH)
+        return enqueue_steps(b, b->stream, Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl);
 
     GraphKey key{Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl, b->form};
     auto it = b->graphs.find(key);
@@ -627,6 +671,7 @@ int fv_batch_launches_per_update(const fv_batch_t *b)
     switch (b->form) {
     case FV_FORM_CASCADE: return 5;
     case FV_FORM_TILE: return 1;
+    case FV_FORM_TASKGRAPH: return b->T * (2 * b->dim + 3);   // kernel nodes of the one graph launch
     default: return b->plan.num_classes;   // one launch per patch-size class (neighbours read in-kernel)
     }
 }
@@ -634,15 +679,17 @@ int fv_batch_launches_per_update(const fv_batch_t *b)
 int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len)
 {
     if (!b || !buf || len == 0) return fail(FV_EINVAL, "NULL argument");
-    const char *form = b->form == FV_FORM_CASCADE ? "cascade" : (b->form == FV_FORM_TILE ? "tile" : "fused");
+    const char *form = b->form == FV_FORM_CASCADE ? "cascade"
+                       : (b->form == FV_FORM_TILE ? "tile" : (b->form == FV_FORM_TASKGRAPH ? "taskgraph" : "fused"));
+    const char *lay = b->cascade_layout == FV_LAYOUT_SOA ? "soa" : (b->cascade_layout == FV_LAYOUT_AOSOA ? "aosoa" : "aos");
     const char *prec = b->precision == FV_F64 ? "f64" : (b->precision == FV_F32 ? "f32" : "bf16/f32");
     const char *fk = b->fused_kernel == fv::FUSED_SWEEP2D ? "sweep2d"
                      : (b->fused_kernel == fv::FUSED_SWEEP3D ? fv::fused3d_kernel_name(b->view, b->precision)
                                                              : "none");
     snprintf(buf, len, "form=%s precision=%s dim=%d patches=%d max_p=%d uniform_p=%d fused_kernel=%s "
-             "items=%d warps_per_block=%d blocks_per_sm=%d scratch_bytes=%zu",
+             "items=%d warps_per_block=%d blocks_per_sm=%d scratch_bytes=%zu cascade_layout=%s",
              form, prec, b->dim, b->T, b->view.max_p, b->view.uniform_p, fk, b->plan.num_items,
-             b->plan.shape.warps_per_block, b->plan.shape.blocks_per_sm, b->scratch_bytes);
+             b->plan.shape.warps_per_block, b->plan.shape.blocks_per_sm, b->scratch_bytes, lay);
     return FV_OK;
 }
 

@@ -18,6 +18,40 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Layout of the per-face and per-volume vector temporaries (F_n and the face
+// fluxes), the ablation of the paper's App. C: element (n, cell, k) of a
+// batch with `total` cells (padded to a multiple of 32 in the scratch).
+//   AoS   [n][cell][k]   the N unknowns of a volume contiguous
+//   SoA   [n][k][cell]   one array per unknown
+//   AoSoA [n][cell/32][k][cell%32]   blocks of 32 volumes, unknown-major
+template <int L> struct Layout;
+template <> struct Layout<CASCADE_AOS> {
+    static __device__ __forceinline__ int64_t at(int n, int64_t cell, int k, int64_t total, int N)
+    {
+        return ((int64_t)n * total + cell) * N + k;
+    }
+};
+template <> struct Layout<CASCADE_SOA> {
+    static __device__ __forceinline__ int64_t at(int n, int64_t cell, int k, int64_t total, int N)
+    {
+        return ((int64_t)n * N + k) * total + cell;
+    }
+};
+template <> struct Layout<CASCADE_AOSOA> {
+    static __device__ __forceinline__ int64_t at(int n, int64_t cell, int k, int64_t total, int N)
+    {
+        return (((int64_t)n * (total >> 5) + (cell >> 5)) * N + k) * 32 + (cell & 31);
+    }
+};
+
+// Cell range and direction of one launch: the whole batch and every axis for
+// the batched realisation, one patch (and one axis for K1/K2) for the
+// task-graph realisation.
+struct Range {
+    int64_t c0, c1;       // cells [c0, c1)
+    int dir;              // axis, or -1 for all
+};
+
 // Decoded halo-inclusive coordinates of a cell of the batch.
 struct CellPos {
     int patch;
@@ -71,21 +105,21 @@ __device__ __forceinline__ const S *volume_ptr(const BatchView &b, const S *q, i
 }
 
 // K1: directional fluxes and eigenvalues of every volume in a face-halo range.
-template <int D, typename S, typename C>
+template <int D, typename S, typename C, int L>
 __global__ void __launch_bounds__(kThreads) k_flux(BatchView b, const S *__restrict__ q,
-                                                   C *__restrict__ fbuf, C *__restrict__ lam)
+                                                   C *__restrict__ fbuf, C *__restrict__ lam, int64_t pad,
+                                                   Range r)
 {
     constexpr int N = D + 2;
     const Gas<C> g{C(b.gamma), C(b.gamma - 1.0)};
-    const int64_t total = b.total_cells;
-    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < total;
+    for (int64_t cell = r.c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < r.c1;
          cell += (int64_t)gridDim.x * blockDim.x) {
         CellPos c = decode<D>(b, cell);
         bool need[D];
         bool any = false;
 #pragma unroll
         for (int n = 0; n < D; ++n) {
-            bool ok = true;
+            bool ok = r.dir < 0 || r.dir == n;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 int v = coord<D>(c, a);
@@ -104,31 +138,29 @@ __global__ void __launch_bounds__(kThreads) k_flux(BatchView b, const S *__restr
             if (!need[n]) continue;
             C F[N];
             flux<D>(qv, s, n, F);
-            C *dst = fbuf + ((int64_t)n * total + cell) * N;
 #pragma unroll
-            for (int k = 0; k < N; ++k) dst[k] = F[k];
-            lam[(int64_t)n * total + cell] = eigenvalue<D>(s, n);
+            for (int k = 0; k < N; ++k) fbuf[Layout<L>::at(n, cell, k, pad, N)] = F[k];
+            lam[(int64_t)n * pad + cell] = eigenvalue<D>(s, n);
         }
     }
 }
 
 // K2: Rusanov flux at the lower face (along n) of every volume whose
 // coordinate along n is in [0, p] and elsewhere in [0, p-1].
-template <int D, typename S, typename C>
+template <int D, typename S, typename C, int L>
 __global__ void __launch_bounds__(kThreads) k_face(BatchView b, const S *__restrict__ q,
                                                    const C *__restrict__ fbuf,
                                                    const C *__restrict__ lam,
-                                                   C *__restrict__ face)
+                                                   C *__restrict__ face, int64_t pad, Range r)
 {
     constexpr int N = D + 2;
-    const int64_t total = b.total_cells;
-    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < total;
+    for (int64_t cell = r.c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < r.c1;
          cell += (int64_t)gridDim.x * blockDim.x) {
         CellPos c = decode<D>(b, cell);
         const int64_t e = c.p + 2;
 #pragma unroll
         for (int n = 0; n < D; ++n) {
-            bool ok = true;
+            bool ok = r.dir < 0 || r.dir == n;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 int v = coord<D>(c, a);
@@ -142,29 +174,28 @@ __global__ void __launch_bounds__(kThreads) k_face(BatchView b, const S *__restr
             C qL[N], qR[N], FL[N], FR[N], Fh[N];
             load_volume<N>(volume_ptr<D>(b, q, c.patch, c.p, xl, yl, zl), qL);
             load_volume<N>(volume_ptr<D>(b, q, c.patch, c.p, c.x, c.y, c.z), qR);
-            const C *fl = fbuf + ((int64_t)n * total + cl) * N;
-            const C *fr = fbuf + ((int64_t)n * total + cell) * N;
 #pragma unroll
-            for (int k = 0; k < N; ++k) { FL[k] = fl[k]; FR[k] = fr[k]; }
-            rusanov2<N>(qL, qR, FL, FR, lam[(int64_t)n * total + cl], lam[(int64_t)n * total + cell], Fh);
-            C *dst = face + ((int64_t)n * total + cell) * N;
+            for (int k = 0; k < N; ++k) {
+                FL[k] = fbuf[Layout<L>::at(n, cl, k, pad, N)];
+                FR[k] = fbuf[Layout<L>::at(n, cell, k, pad, N)];
+            }
+            rusanov2<N>(qL, qR, FL, FR, lam[(int64_t)n * pad + cl], lam[(int64_t)n * pad + cell], Fh);
 #pragma unroll
-            for (int k = 0; k < N; ++k) dst[k] = Fh[k];
+            for (int k = 0; k < N; ++k) face[Layout<L>::at(n, cell, k, pad, N)] = Fh[k];
         }
     }
 }
 
 // K3: volume update of every interior volume.
-template <int D, typename S, typename C>
+template <int D, typename S, typename C, int L>
 __global__ void __launch_bounds__(kThreads) k_update(BatchView b, const S *__restrict__ q,
                                                      S *__restrict__ qout,
                                                      const C *__restrict__ face,
                                                      const double *__restrict__ dx,
-                                                     const double *__restrict__ dt)
+                                                     const double *__restrict__ dt, int64_t pad, Range r)
 {
     constexpr int N = D + 2;
-    const int64_t total = b.total_cells;
-    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < total;
+    for (int64_t cell = r.c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < r.c1;
          cell += (int64_t)gridDim.x * blockDim.x) {
         CellPos c = decode<D>(b, cell);
         bool interior = c.x >= 0 && c.x < c.p && c.y >= 0 && c.y < c.p &&
@@ -177,10 +208,9 @@ __global__ void __launch_bounds__(kThreads) k_update(BatchView b, const S *__res
 #pragma unroll
         for (int n = 0; n < D; ++n) {
             const int64_t stride = n == 0 ? 1 : (n == 1 ? e : e * e);
-            const C *fl = face + ((int64_t)n * total + cell) * N;
-            const C *fr = face + ((int64_t)n * total + cell + stride) * N;
 #pragma unroll
-            for (int k = 0; k < N; ++k) acc[k] += fr[k] - fl[k];
+            for (int k = 0; k < N; ++k)
+                acc[k] += face[Layout<L>::at(n, cell + stride, k, pad, N)] - face[Layout<L>::at(n, cell, k, pad, N)];
         }
         const double h = __ldg(dx + c.patch), tau = __ldg(dt + c.patch);
         const C s = C(tau / (2.0 * h));
@@ -196,12 +226,12 @@ __global__ void __launch_bounds__(kThreads) k_update(BatchView b, const S *__res
 // K4: max eigenvalue of every interior volume of the new state.
 template <int D, typename S, typename C>
 __global__ void __launch_bounds__(kThreads) k_lambda(BatchView b, const S *__restrict__ q,
-                                                     C *__restrict__ lam_new)
+                                                     C *__restrict__ lam_new, Range r)
 {
     constexpr int N = D + 2;
     const Gas<C> g{C(b.gamma), C(b.gamma - 1.0)};
     bool bad = false;
-    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < b.total_cells;
+    for (int64_t cell = r.c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < r.c1;
          cell += (int64_t)gridDim.x * blockDim.x) {
         CellPos c = decode<D>(b, cell);
         bool interior = c.x >= 0 && c.x < c.p && c.y >= 0 && c.y < c.p &&
@@ -222,10 +252,10 @@ template <int D, typename C>
 __global__ void __launch_bounds__(kThreads) k_reduce(BatchView b, const C *__restrict__ lam_new,
                                                      const double *__restrict__ dx, double cfl,
                                                      double *__restrict__ lambda_out,
-                                                     double *__restrict__ dt_next_out)
+                                                     double *__restrict__ dt_next_out, int first_patch)
 {
     __shared__ C red[32];
-    const int i = blockIdx.x;
+    const int i = first_patch + blockIdx.x;
     const int p = __ldg(b.psize + i);
     const int64_t e = p + 2;
     const int64_t base = __ldg(b.cell_off + i);
@@ -256,10 +286,14 @@ int grid_for(int64_t work)
 
 }  // namespace
 
+// cells of the scratch arrays: the batch's cells rounded up to whole blocks
+// of 32 (the AoSoA layout's block)
+int64_t cascade_pad(const BatchView &b) { return (b.total_cells + 31) & ~int64_t(31); }
+
 size_t cascade_scratch_bytes(const BatchView &b, int precision)
 {
     size_t cs = precision == PREC_F64 ? 8 : 4;
-    size_t N = b.dim + 2, M = (size_t)b.total_cells;
+    size_t N = b.dim + 2, M = (size_t)cascade_pad(b);
     size_t bytes = 0;
     bytes += (size_t)b.dim * M * N * cs;   // flux
     bytes += 256;
@@ -274,7 +308,7 @@ size_t cascade_scratch_bytes(const BatchView &b, int precision)
 void cascade_scratch_carve(void *base, const BatchView &b, int precision, CascadeScratch *s)
 {
     size_t cs = precision == PREC_F64 ? 8 : 4;
-    size_t N = b.dim + 2, M = (size_t)b.total_cells;
+    size_t N = b.dim + 2, M = (size_t)cascade_pad(b);
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
     char *p = static_cast<char *>(base);
     s->flux = p;
@@ -286,10 +320,13 @@ void cascade_scratch_carve(void *base, const BatchView &b, int precision, Cascad
     s->lam_new = p;
 }
 
-cudaError_t launch_cascade_update(const BatchView &b, int precision, const StepArgs &a,
-                                  const CascadeScratch &s, cudaStream_t st)
+template <int L>
+cudaError_t launch_cascade_layout(const BatchView &b, int precision, const StepArgs &a, const CascadeScratch &s,
+                                  cudaStream_t st)
 {
     const int grid = grid_for(b.total_cells);
+    const int64_t pad = cascade_pad(b);
+    const Range all{0, b.total_cells, -1};
     FV_DISPATCH(b.dim, precision, {
         using C = typename StorageTraits<S>::Compute;
         const S *q = static_cast<const S *>(a.q_in);
@@ -298,16 +335,105 @@ cudaError_t launch_cascade_update(const BatchView &b, int precision, const StepA
         C *lm = static_cast<C *>(s.lam);
         C *fc = static_cast<C *>(s.face);
         C *ln = static_cast<C *>(s.lam_new);
-        k_flux<D, S, C><<<grid, kThreads, 0, st>>>(b, q, fl, lm);
-        k_face<D, S, C><<<grid, kThreads, 0, st>>>(b, q, fl, lm, fc);
-        k_update<D, S, C><<<grid, kThreads, 0, st>>>(b, q, qo, fc, a.dx, a.dt);
+        k_flux<D, S, C, L><<<grid, kThreads, 0, st>>>(b, q, fl, lm, pad, all);
+        k_face<D, S, C, L><<<grid, kThreads, 0, st>>>(b, q, fl, lm, fc, pad, all);
+        k_update<D, S, C, L><<<grid, kThreads, 0, st>>>(b, q, qo, fc, a.dx, a.dt, pad, all);
         if (a.lambda_out || a.dt_next_out) {
-            k_lambda<D, S, C><<<grid, kThreads, 0, st>>>(b, qo, ln);
+            k_lambda<D, S, C><<<grid, kThreads, 0, st>>>(b, qo, ln, all);
             k_reduce<D, C><<<b.num_patches, kThreads, 0, st>>>(b, ln, a.dx, a.cfl, a.lambda_out,
-                                                               a.dt_next_out);
+                                                               a.dt_next_out, 0);
         }
     });
     return cudaGetLastError();
+}
+
+// One kernel node of the task graph.
+cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *deps, size_t ndeps, void *func,
+                       int grid, void **args)
+{
+    cudaKernelNodeParams np{};
+    np.func = func;
+    np.gridDim = dim3((unsigned)grid);
+    np.blockDim = dim3(kThreads);
+    np.sharedMemBytes = 0;
+    np.kernelParams = args;
+    np.extra = nullptr;
+    return cudaGraphAddKernelNode(node, g, deps, ndeps, &np);
+}
+
+// The paper's task-graph realisation (Sec. 3): per patch, one node per
+// algorithmic step and axis, linked by their data dependencies only:
+//   K1(n) -> K2(n) for every axis n (the axes run concurrently),
+//   all K2(n) -> K3 -> K4 -> K5 (one block).
+// Patches share no edge, so the graph exposes all patch-level parallelism;
+// each node runs the batched realisation's kernel restricted to the
+// patch's cells (and axis), so results are bitwise those of the batched form.
+template <int L>
+cudaError_t build_taskgraph_layout(const BatchView &bv, const int64_t *cell_off, int precision, const StepArgs &a,
+                                   const CascadeScratch &sc, cudaGraph_t g)
+{
+    BatchView b = bv;
+    int64_t pad = cascade_pad(b);
+    const double *dx = a.dx, *dt = a.dt;
+    double *lam_out = a.lambda_out, *dt_next = a.dt_next_out;
+    double cfl = a.cfl;
+    cudaError_t e = cudaSuccess;
+    FV_DISPATCH(b.dim, precision, {
+        using C = typename StorageTraits<S>::Compute;
+        const S *q = static_cast<const S *>(a.q_in);
+        S *qo = static_cast<S *>(a.q_out);
+        C *fl = static_cast<C *>(sc.flux);
+        C *lm = static_cast<C *>(sc.lam);
+        C *fc = static_cast<C *>(sc.face);
+        C *ln = static_cast<C *>(sc.lam_new);
+        for (int i = 0; i < b.num_patches && e == cudaSuccess; ++i) {
+            Range r{cell_off[i], cell_off[i + 1], -1};
+            const int grid = (int)((r.c1 - r.c0 + kThreads - 1) / kThreads);
+            cudaGraphNode_t faces[3];
+            for (int n = 0; n < D && e == cudaSuccess; ++n) {
+                Range rn{r.c0, r.c1, n};
+                cudaGraphNode_t fnode;
+                void *fargs[] = {&b, &q, &fl, &lm, &pad, &rn};
+                e = add_kernel(g, &fnode, nullptr, 0, (void *)k_flux<D, S, C, L>, grid, fargs);
+                if (e != cudaSuccess) break;
+                void *cargs[] = {&b, &q, &fl, &lm, &fc, &pad, &rn};
+                e = add_kernel(g, &faces[n], &fnode, 1, (void *)k_face<D, S, C, L>, grid, cargs);
+            }
+            if (e != cudaSuccess) break;
+            cudaGraphNode_t un;
+            void *uargs[] = {&b, &q, &qo, &fc, &dx, &dt, &pad, &r};
+            e = add_kernel(g, &un, faces, D, (void *)k_update<D, S, C, L>, grid, uargs);
+            if (e != cudaSuccess || !(lam_out || dt_next)) continue;
+            cudaGraphNode_t ln_node, rd;
+            void *largs[] = {&b, &qo, &ln, &r};
+            e = add_kernel(g, &ln_node, &un, 1, (void *)k_lambda<D, S, C>, grid, largs);
+            if (e != cudaSuccess) break;
+            int first = i;
+            void *rargs[] = {&b, &ln, &dx, &cfl, &lam_out, &dt_next, &first};
+            e = add_kernel(g, &rd, &ln_node, 1, (void *)k_reduce<D, C>, 1, rargs);
+        }
+    });
+    return e;
+}
+
+cudaError_t build_cascade_taskgraph(const BatchView &b, const int64_t *cell_off_host, int precision,
+                                    const StepArgs &a, const CascadeScratch &s, int layout, cudaGraph_t g)
+{
+    switch (layout) {
+    case CASCADE_SOA: return build_taskgraph_layout<CASCADE_SOA>(b, cell_off_host, precision, a, s, g);
+    case CASCADE_AOSOA: return build_taskgraph_layout<CASCADE_AOSOA>(b, cell_off_host, precision, a, s, g);
+    default: return build_taskgraph_layout<CASCADE_AOS>(b, cell_off_host, precision, a, s, g);
+    }
+}
+
+cudaError_t launch_cascade_update(const BatchView &b, int precision, const StepArgs &a,
+                                  const CascadeScratch &s, cudaStream_t st, int layout)
+{
+    switch (layout) {
+    case CASCADE_SOA: return launch_cascade_layout<CASCADE_SOA>(b, precision, a, s, st);
+    case CASCADE_AOSOA: return launch_cascade_layout<CASCADE_AOSOA>(b, precision, a, s, st);
+    default: return launch_cascade_layout<CASCADE_AOS>(b, precision, a, s, st);
+    }
 }
 
 }  // namespace fv

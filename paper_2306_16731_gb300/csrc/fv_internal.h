@@ -82,9 +82,16 @@ struct FusedPlan {
 
 enum FusedKernel { FUSED_NONE = 0, FUSED_SWEEP2D = 1, FUSED_SWEEP3D = 2 };
 
+// Layout of the loop cascade's vector temporaries (F_n, face fluxes).
+enum CascadeLayout { CASCADE_AOS = 0, CASCADE_SOA = 1, CASCADE_AOSOA = 2 };
+
 // All launchers return cudaSuccess or the launch error; they never sync.
 cudaError_t launch_cascade_update(const BatchView &b, int precision, const StepArgs &a,
-                                  const CascadeScratch &s, cudaStream_t st);
+                                  const CascadeScratch &s, cudaStream_t st, int layout);
+// Add the task-graph realisation of one update (per-patch nodes of the
+// cascade's kernels) to graph g; cell_off_host has T+1 entries.
+cudaError_t build_cascade_taskgraph(const BatchView &b, const int64_t *cell_off_host, int precision,
+                                    const StepArgs &a, const CascadeScratch &s, int layout, cudaGraph_t g);
 cudaError_t launch_tile_update(const BatchView &b, int precision, const StepArgs &a,
                                cudaStream_t st);
 bool tile_supported(const BatchView &b, int precision);

@@ -156,7 +156,7 @@ extern "C" int fv_patch_batch_update_noalloc(int dim, int num_patches, int patch
     fv::CascadeScratch cs{};
     fv::cascade_scratch_carve(base + off_cascade, v, precision, &cs);
     fv::StepArgs a{Q_in, Q_out, dx, dt, lambda_out, dt_next_out, cfl};
-    e = fv::launch_cascade_update(v, precision, a, cs, st);
+    e = fv::launch_cascade_update(v, precision, a, cs, st, fv::CASCADE_AOS);
     if (e != cudaSuccess) return noalloc_fail(FV_ECUDA, cudaGetErrorString(e));
     return FV_OK;
 }

@@ -34,6 +34,10 @@ FV_HALO_PERIODIC = 1
 FV_FORM_FUSED = 0
 FV_FORM_CASCADE = 1
 FV_FORM_TILE = 2
+FV_FORM_TASKGRAPH = 3
+FV_LAYOUT_AOS = 0
+FV_LAYOUT_SOA = 1
+FV_LAYOUT_AOSOA = 2
 
 _ERRNAMES = {FV_EINVAL: "FV_EINVAL", FV_ENOMEM: "FV_ENOMEM", FV_ECUDA: "FV_ECUDA",
              FV_EUNSUPPORTED: "FV_EUNSUPPORTED", FV_ENONPHYSICAL: "FV_ENONPHYSICAL",
@@ -45,7 +49,7 @@ EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_ba
            "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
            "fv_batch_scratch_bytes", "fv_batch_describe", "fv_batch_launches_per_update",
-           "fv_batch_test_wait_expiry"]
+           "fv_batch_test_wait_expiry", "fv_batch_set_cascade_layout"]
 
 
 class FVError(RuntimeError):
@@ -83,6 +87,7 @@ def load() -> ctypes.CDLL:
             "fv_batch_set_stream": (i, [_vp, _vp]),
             "fv_batch_set_launch_shape": (i, [_vp, i, i]),
             "fv_batch_test_wait_expiry": (i, [_vp, i]),
+            "fv_batch_set_cascade_layout": (i, [_vp, i]),
             "fv_batch_set_neighbours": (i, [_vp, ctypes.POINTER(ctypes.c_int32)]),
             "fv_patch_batch_update_host": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, d, i]),
             "fv_halo_exchange": (i, [_vp, _vp]),
@@ -162,6 +167,10 @@ def fv_halo_exchange(b, Q):
 
 def fv_batch_set_launch_shape(b, warps_per_block, blocks_per_sm):
     return _check(load().fv_batch_set_launch_shape(b, int(warps_per_block), int(blocks_per_sm)))
+
+
+def fv_batch_set_cascade_layout(b, layout):
+    return _check(load().fv_batch_set_cascade_layout(b, int(layout)))
 
 
 def fv_batch_test_wait_expiry(b, enable):
@@ -274,6 +283,10 @@ class FVBatch:
 
     def set_launch_shape(self, warps_per_block, blocks_per_sm):
         fv_batch_set_launch_shape(self.handle, warps_per_block, blocks_per_sm)
+
+    def set_cascade_layout(self, layout):
+        """Layout of the cascade's (and task graph's) vector temporaries (FV_LAYOUT_*)."""
+        fv_batch_set_cascade_layout(self.handle, layout)
 
     def test_wait_expiry(self, enable):
         """Test hook: make the bounded copy waits of the periodic 8^3 kernel run out."""

@@ -606,3 +606,70 @@ def test_bounded_copy_wait_reports_timeout_and_context_survives():
                                      halo_mode=inputs.PERIODIC)
     assert batch_rel_linf(qb.to(torch.float64).cpu().numpy(), ref, 3, w.patch_size) < 1e-5
     b.close()
+
+
+def _one_update(w, precision, form, layout=0, dt=1e-3):
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    T = w.num_patches
+    b = fb.FVBatch(w.dim, w.patch_size, precision=precision, halo_mode=w.halo_mode, form=form)
+    b.set_cascade_layout(layout)
+    qa = to_device(w.Q0, precision)
+    qb = qa.clone()
+    dx = torch.tensor(np.asarray(w.dx, dtype=np.float64), device="cuda")
+    dtv = torch.full((T,), dt, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dtn = torch.zeros_like(lam)
+    b.update(qa, qb, dx, dtv, lam, dtn, 0.4)
+    b.status()
+    desc = b.describe()
+    out = (qb.to(torch.float64).cpu().numpy(), lam.cpu().numpy(), dtn.cpu().numpy(), desc)
+    b.close()
+    return out
+
+
+@pytest.mark.parametrize("dim,sizes,halo", [(2, [3, 16, 5, 8, 1, 32, 7] * 3, inputs.FIXED),
+                                            (2, [16] * 40, inputs.PERIODIC),
+                                            (3, [4, 8, 3, 6] * 3, inputs.FIXED),
+                                            (3, [8] * 9, inputs.PERIODIC)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cascade_temporaries_layout_does_not_change_bits(dim, sizes, halo, precision):
+    """AoS, SoA and AoSoA temporaries (the paper's App. C ablation) store the
+    same values in different places: the update is bitwise identical."""
+    w = inputs.uniform_batch(dim, sizes, seed=101 + dim, dx=0.05, halo_mode=halo)
+    ref = _one_update(w, precision, FORMS["cascade"], 0)
+    for layout in (1, 2):
+        got = _one_update(w, precision, FORMS["cascade"], layout)
+        assert ("cascade_layout=%s" % ("soa" if layout == 1 else "aosoa")) in got[3]
+        for a, b in zip(got[:3], ref[:3]):
+            assert np.array_equal(a, b)
+    # and it is the right update
+    q0 = initial_fp64(w.Q0, precision)
+    oref, lref = oracle.batch_step(dim, w.patch_size, w.dx, [1e-3] * w.num_patches, q0, halo_mode=halo)
+    assert batch_rel_linf(ref[0], oref, dim, w.patch_size) < TOL[precision]
+
+
+@pytest.mark.parametrize("dim,sizes,halo", [(2, [3, 16, 5, 8, 1, 32, 7] * 2, inputs.FIXED),
+                                            (2, [8] * 30, inputs.PERIODIC),
+                                            (3, [4, 8, 3, 6, 5], inputs.FIXED),
+                                            (3, [6] * 7, inputs.PERIODIC)])
+@pytest.mark.parametrize("precision,layout", [(0, 0), (1, 0), (0, 1), (1, 2)])
+def test_taskgraph_form_is_bitwise_the_batched_cascade(dim, sizes, halo, precision, layout):
+    """The task-graph realisation runs the batched kernels restricted to one
+    patch (and axis) per node, so its state, eigenvalues and time steps are
+    bitwise those of the batched realisation."""
+    w = inputs.uniform_batch(dim, sizes, seed=111 + dim, dx=0.05, halo_mode=halo)
+    ref = _one_update(w, precision, FORMS["cascade"], layout)
+    got = _one_update(w, precision, 3, layout)
+    assert "form=taskgraph" in got[3]
+    for a, b in zip(got[:3], ref[:3]):
+        assert np.array_equal(a, b)
+
+
+def test_taskgraph_form_multi_step_run_equals_cascade():
+    """fv_batch_run with the task-graph form (one graph launch per step; a
+    requested outer graph is not captured) chains CFL steps like the cascade."""
+    w = inputs.uniform_batch(2, [8, 16, 4] * 10, seed=121, dx=0.02)
+    a = gpu_run(w, 0, FORMS["cascade"], 5)
+    b = gpu_run(w, 0, 3, 5, use_graph=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])

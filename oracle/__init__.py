@@ -14,6 +14,8 @@ from .fv_oracle import (  # noqa: F401
     batch_run,
     batch_totals,
     halo_exchange,
+    swe_batch_step,
+    swe_batch_max_eigenvalue,
     num_threads,
     set_num_threads,
     FIXED,

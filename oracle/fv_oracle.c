@@ -465,3 +465,159 @@ int fvo_halo_exchange(int dim, int T, const int32_t *p, const int32_t *nbr, doub
     free(off);
     return FVO_OK;
 }
+
+/* =====================================================================
+ * Generic first-order hyperbolic PDE of Eq. 1,
+ *     dQ/dt + div F(Q) + sum_n B_n(Q) dQ/dx_n = S(Q),
+ * realised for the two-dimensional shallow water equations over a
+ * bathymetry b with a Coriolis force (the paper states the PDE class in
+ * Sec. 2 and studies only Euler, for which B = 0 and S = 0):
+ *     Q = (h, hu, hv, b),  b a parameter (db/dt = 0), u = hu/h, v = hv/h,
+ *     F_x = (hu, hu u + g h^2 / 2, hv u, 0),
+ *     F_y = (hv, hu v, hv v + g h^2 / 2, 0),
+ *     B_x(Q) dQ/dx = (0, g h db/dx, 0, 0),  B_y(Q) dQ/dy = (0, 0, g h db/dy, 0),
+ *     S(Q) = (0, f hv, -f hu, 0),
+ *     lambda_n = |u_n| + sqrt(g h).
+ * Readings (the paper gives no discretisation of B and S):
+ *   R13 the Rusanov flux of Eq. 2 (reading R3) acts on the evolved unknowns
+ *       (h, hu, hv); the parameter b gets no flux and no dissipation and is
+ *       copied unchanged;
+ *   R14 the non-conservative product at a face L|R along n is
+ *       D = B_n(Qbar) (Q_R - Q_L) with Qbar = (Q_L + Q_R) / 2, and half of it
+ *       enters each of the two volumes;
+ *   R15 the source is explicit and pointwise, evaluated on the old state.
+ * One step of an interior volume c (faces l = c-1/2, r = c+1/2 along n):
+ *     acc = sum_{n = x, y} ((Fhat_r - Fhat_l) + 1/2 (D_r + D_l)),
+ *     Q_new = Q - (dt / h) acc + dt S(Q).
+ * Halos follow R7.  The CFL step uses lambda_max as in R5/R6.
+ * ===================================================================== */
+
+#define SWE_N 4
+
+static double swe_lambda(double g, const double *q, int n)
+{
+    double h = q[0];
+    return fabs(q[1 + n] / h) + sqrt(g * h);
+}
+
+static void swe_flux(double g, const double *q, int n, double *F)
+{
+    double h = q[0], un = q[1 + n] / h;
+    F[0] = q[1 + n];
+    F[1] = q[1] * un + (n == 0 ? 0.5 * g * h * h : 0.0);
+    F[2] = q[2] * un + (n == 1 ? 0.5 * g * h * h : 0.0);
+    F[3] = 0.0;
+}
+
+/* D = B_n(Qbar) (Q_R - Q_L) (reading R14). */
+static void swe_ncp(double g, const double *QL, const double *QR, int n, double *D)
+{
+    double hbar = 0.5 * (QL[0] + QR[0]);
+    D[0] = 0.0;
+    D[1] = n == 0 ? g * hbar * (QR[3] - QL[3]) : 0.0;
+    D[2] = n == 1 ? g * hbar * (QR[3] - QL[3]) : 0.0;
+    D[3] = 0.0;
+}
+
+/* Rusanov flux on the evolved unknowns (readings R3, R13). */
+static void swe_face(double g, const double *QL, const double *QR, int n, double *Fhat)
+{
+    double FL[SWE_N], FR[SWE_N];
+    swe_flux(g, QL, n, FL);
+    swe_flux(g, QR, n, FR);
+    double lL = swe_lambda(g, QL, n), lR = swe_lambda(g, QR, n);
+    double lam = lL > lR ? lL : lR;
+    for (int k = 0; k < 3; ++k)
+        Fhat[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * lam * (QR[k] - QL[k]);
+    Fhat[3] = 0.0;
+}
+
+static double swe_patch_max_eigenvalue(int p, double g, const double *Q)
+{
+    double lam = 0.0;
+    for (int j = 0; j < p; ++j)
+        for (int i = 0; i < p; ++i) {
+            const double *q = Q + cell_index(2, p, i, j, 0) * SWE_N;
+            for (int n = 0; n < 2; ++n) {
+                double l = swe_lambda(g, q, n);
+                if (l > lam) lam = l;
+            }
+        }
+    return lam;
+}
+
+static int swe_patch_step(int p, double g, double f, int periodic, double h, double dt,
+                          const double *Qin, double *Qout)
+{
+    int64_t nc = patch_cells(2, p);
+    double *Q = (double *)malloc((size_t)(nc * SWE_N) * sizeof(double));
+    if (!Q) return FVO_ENOMEM;
+    memcpy(Q, Qin, (size_t)(nc * SWE_N) * sizeof(double));
+    if (periodic)
+        fill_periodic_halo(2, p, SWE_N, Q);
+    memcpy(Qout, Q, (size_t)(nc * SWE_N) * sizeof(double));
+    double scale = dt / h;
+    for (int j = 0; j < p; ++j)
+        for (int i = 0; i < p; ++i) {
+            int64_t c = cell_index(2, p, i, j, 0);
+            const double *qc = Q + c * SWE_N;
+            double acc[SWE_N] = {0, 0, 0, 0};
+            for (int n = 0; n < 2; ++n) {
+                int lo[2] = {i, j}, hi[2] = {i, j};
+                lo[n] -= 1;
+                hi[n] += 1;
+                const double *ql = Q + cell_index(2, p, lo[0], lo[1], 0) * SWE_N;
+                const double *qr = Q + cell_index(2, p, hi[0], hi[1], 0) * SWE_N;
+                double Fl[SWE_N], Fr[SWE_N], Dl[SWE_N], Dr[SWE_N];
+                swe_face(g, ql, qc, n, Fl);
+                swe_face(g, qc, qr, n, Fr);
+                swe_ncp(g, ql, qc, n, Dl);
+                swe_ncp(g, qc, qr, n, Dr);
+                for (int k = 0; k < SWE_N; ++k)
+                    acc[k] += (Fr[k] - Fl[k]) + 0.5 * (Dr[k] + Dl[k]);
+            }
+            double S[SWE_N] = {0.0, f * qc[2], -f * qc[1], 0.0};
+            for (int k = 0; k < 3; ++k)
+                Qout[c * SWE_N + k] = qc[k] - scale * acc[k] + dt * S[k];
+            Qout[c * SWE_N + 3] = qc[3];
+        }
+    free(Q);
+    return FVO_OK;
+}
+
+/* One shallow water step over a batch of 2D patches (N = 4 unknowns per
+ * volume, layout as for Euler); lambda_out (may be NULL) = maximum
+ * eigenvalue of the new state per patch. */
+int fvo_swe_batch_step(int T, const int32_t *p, const double *dx, const double *dt, double g, double f,
+                       int halo_mode, const double *Qin, double *Qout, double *lambda_out)
+{
+    int rc = check_batch(2, T, p);
+    if (rc) return rc;
+    int64_t *off = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
+    if (!off) return FVO_ENOMEM;
+    off[0] = 0;
+    for (int i = 0; i < T; ++i) off[i + 1] = off[i] + SWE_N * patch_cells(2, p[i]);
+    int err = FVO_OK;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) reduction(min : err)
+#endif
+    for (int i = 0; i < T; ++i) {
+        int r = swe_patch_step(p[i], g, f, halo_mode == 1, dx[i], dt[i], Qin + off[i], Qout + off[i]);
+        if (r < err) err = r;
+        if (lambda_out) lambda_out[i] = swe_patch_max_eigenvalue(p[i], g, Qout + off[i]);
+    }
+    free(off);
+    return err;
+}
+
+int fvo_swe_batch_max_eigenvalue(int T, const int32_t *p, double g, const double *Q, double *lambda_out)
+{
+    int rc = check_batch(2, T, p);
+    if (rc) return rc;
+    int64_t o = 0;
+    for (int i = 0; i < T; ++i) {
+        lambda_out[i] = swe_patch_max_eigenvalue(p[i], g, Q + o);
+        o += SWE_N * patch_cells(2, p[i]);
+    }
+    return FVO_OK;
+}

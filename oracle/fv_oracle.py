@@ -72,6 +72,11 @@ def bind(path: str):
                                   ctypes.c_int, _dp, _dp, _dp]
     lib.fvo_batch_totals.restype = ctypes.c_int
     lib.fvo_batch_totals.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, _dp]
+    lib.fvo_swe_batch_step.restype = ctypes.c_int
+    lib.fvo_swe_batch_step.argtypes = [ctypes.c_int, _ip, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, _dp, _dp, _dp]
+    lib.fvo_swe_batch_max_eigenvalue.restype = ctypes.c_int
+    lib.fvo_swe_batch_max_eigenvalue.argtypes = [ctypes.c_int, _ip, ctypes.c_double, _dp, _dp]
     lib.fvo_halo_exchange.restype = ctypes.c_int
     lib.fvo_halo_exchange.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _ip, _dp]
     lib.fvo_num_threads.restype = ctypes.c_int
@@ -229,3 +234,24 @@ def num_threads() -> int:
 def set_num_threads(n: int) -> None:
     """Run the following batch loops on n threads (n < 1: the default)."""
     _load().fvo_set_num_threads(int(n))
+
+
+def swe_batch_step(patch_size, dx, dt, Q, g=9.81, f=0.0, halo_mode=FIXED):
+    """One shallow water step (Eq. 1 with B and S, readings R13-R15) over a
+    batch of 2D patches of Q = (h, hu, hv, b); returns (Q_new, lambda_new)."""
+    p = _i32(patch_size)
+    T = len(p)
+    Q = _f64(Q)
+    out = np.empty_like(Q)
+    lam = np.empty(T)
+    _check(_load().fvo_swe_batch_step(T, _ptr_i(p), _ptr_d(_f64(dx)), _ptr_d(_f64(dt)), float(g), float(f),
+                                      int(halo_mode), _ptr_d(Q), _ptr_d(out), _ptr_d(lam)), "swe_batch_step")
+    return out, lam
+
+
+def swe_batch_max_eigenvalue(patch_size, Q, g=9.81):
+    p = _i32(patch_size)
+    lam = np.empty(len(p))
+    _check(_load().fvo_swe_batch_max_eigenvalue(len(p), _ptr_i(p), float(g), _ptr_d(_f64(Q)), _ptr_d(lam)),
+           "swe_batch_max_eigenvalue")
+    return lam

@@ -596,6 +596,26 @@ def other_workloads(dev, stream, flush_l2, steps):
         "launches_per_step": b.launches_per_update(), "kernel": b.describe()}
     b.close()
     del qs
+    # the generic-PDE kernel (Eq. 1 with non-conservative product and
+    # source): 2D shallow water, 16,384 patches of 16x16, FP32 and FP64
+    for name, prec, es in (("2d_p16_T16384_shallow_water_f32", 1, 4), ("2d_p16_T16384_shallow_water_f64", 0, 8)):
+        ws = inputs.shallow_water_batch([16] * 16384, seed=9, dx=0.01)
+        bs = fb.FVBatch(2, ws.patch_size, precision=prec, pde=fb.FV_PDE_SHALLOW_WATER, params=[9.81, 0.5],
+                        stream=stream.cuda_stream)
+        dtype = torch.float32 if prec == 1 else torch.float64
+        qs = [torch.from_numpy(ws.Q0).to(device=dev).to(dtype), None]
+        qs[1] = qs[0].clone()
+        dx = torch.tensor(ws.dx, device=dev)
+        lam = torch.zeros(ws.num_patches, dtype=torch.float64, device=dev)
+        dts = [torch.zeros_like(lam), torch.zeros_like(lam)]
+        bs.max_eigenvalue(qs[0], lam)
+        bs.cfl_time_step(lam, dx, 0.4, dts[0])
+        ms = single_steps(bs, qs, dx, lam, dts, k, 0.4)
+        bpv = bytes_per_volume(ws, es)
+        res[name] = {"value": ws.interior_volumes / (ms / 1e3), "ms_per_step": ms, "bytes_per_volume": bpv,
+                     "roofline_frac": ws.interior_volumes * bpv / (ms / 1e3) / 1e9 / peak, "kernel": bs.describe()}
+        bs.close()
+        del qs
     # the 2D batch wired as a periodic 128 x 128 grid of patches: halos filled
     # from neighbours in-kernel (fused) vs a separate exchange launch + update
     w2 = inputs.config(2, dtype=np.float32)

@@ -86,6 +86,14 @@ enum {
                                new values (fused kernels write rows whole, x-halo volumes included) */
 };
 
+/* PDE of the batch (Eq. 1: dQ/dt + div F(Q) + sum_n B_n(Q) dQ/dx_n = S(Q)). */
+enum {
+    FV_PDE_EULER = 0,          /* compressible Euler (Sec. 5), N = dim + 2; parameter: gamma */
+    FV_PDE_SHALLOW_WATER = 1   /* 2D shallow water over a bathymetry with Coriolis force, Q = (h, hu, hv, b),
+                                  N = 4, b a parameter; parameters: gravity g, Coriolis f; non-conservative
+                                  product g h grad b and source (0, f hv, -f hu, 0) */
+};
+
 /* Kernel realisation (Sec. 3). */
 enum {
     FV_FORM_FUSED = 0,      /* default: one fused launch per step (warp-level sweep kernels) */
@@ -112,6 +120,22 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches,
                     const int32_t *patch_size, int halo, int unknowns,
                     int precision, int halo_mode, double gamma,
                     void *cuda_stream);
+
+/*
+ * Create a batch for one of the FV_PDE_* systems (Eq. 1; the paper studies
+ * Euler only, Sec. 5).  params holds num_params values: Euler {gamma} (this
+ * is fv_batch_create); shallow water {g > 0, f}, dim must be 2, precision
+ * FV_F64 or FV_F32.  Other PDEs than Euler run on a generic patch-wise
+ * kernel (FV_FORM_TILE, the only form set_form accepts for them): at each
+ * face the Rusanov flux of Eq. 2 on the evolved unknowns and the
+ * non-conservative product B_n((Q_L+Q_R)/2)(Q_R - Q_L), half to each side;
+ * Q_new = Q - dt/h sum_n [(Fhat_r - Fhat_l) + (D_r + D_l)/2] + dt S(Q);
+ * parameter unknowns (b) are copied.  Layout, halos, dx/dt/lambda/dt_next,
+ * status, graphs and host updates work as for Euler.  FV_EINVAL for bad
+ * arguments, FV_EUNSUPPORTED for an unsupported precision or patch size.
+ */
+int fv_batch_create_pde(fv_batch_t **out, int pde, int dim, int num_patches, const int32_t *patch_size,
+                        int precision, int halo_mode, const double *params, int num_params, void *cuda_stream);
 
 /* Select the kernel realisation (FV_FORM_*).  FV_EUNSUPPORTED if this
  * build has no kernel of that form for the batch's shapes; the previous

@@ -200,9 +200,9 @@ extern "C" {
 
 const char *fv_last_error(void) { return g_last_error.c_str(); }
 
-int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *patch_size,
-                    int halo, int unknowns, int precision, int halo_mode, double gamma,
-                    void *cuda_stream)
+static int create_batch(fv_batch_t **out, int pde, int dim, int num_patches, const int32_t *patch_size,
+                        int halo, int unknowns, int precision, int halo_mode, double p0, double p1,
+                        void *cuda_stream)
 {
     g_last_error.clear();
     if (!out) return fail(FV_EINVAL, "out is NULL");
@@ -211,11 +211,22 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     if (num_patches < 0) return fail(FV_EINVAL, "num_patches must be >= 0 (got %d)", num_patches);
     if (num_patches > 0 && !patch_size) return fail(FV_EINVAL, "patch_size is NULL");
     if (halo != 1) return fail(FV_EINVAL, "halo width must be 1 (got %d)", halo);
-    if (unknowns != dim + 2) return fail(FV_EINVAL, "Euler in %dD has %d unknowns (got %d)", dim, dim + 2, unknowns);
     if (precision < FV_F64 || precision > FV_BF16_F32) return fail(FV_EINVAL, "unknown precision %d", precision);
     if (halo_mode != FV_HALO_FIXED && halo_mode != FV_HALO_PERIODIC)
         return fail(FV_EINVAL, "unknown halo mode %d", halo_mode);
-    if (!(gamma > 1.0) || !(gamma < 1e300)) return fail(FV_EINVAL, "gamma must be finite and > 1");
+    const double gamma = pde == FV_PDE_EULER ? p0 : 1.4;
+    if (pde == FV_PDE_EULER) {
+        if (unknowns != dim + 2) return fail(FV_EINVAL, "Euler in %dD has %d unknowns (got %d)", dim, dim + 2, unknowns);
+        if (!(gamma > 1.0) || !(gamma < 1e300)) return fail(FV_EINVAL, "gamma must be finite and > 1");
+    } else if (pde == FV_PDE_SHALLOW_WATER) {
+        if (dim != 2) return fail(FV_EINVAL, "the shallow water equations are two-dimensional (got dim %d)", dim);
+        if (unknowns != 4) return fail(FV_EINVAL, "shallow water has 4 unknowns (h, hu, hv, b)");
+        if (precision == FV_BF16_F32) return fail(FV_EUNSUPPORTED, "shallow water: FP64 or FP32 storage only");
+        if (!(p0 > 0.0) || !(p0 < 1e300)) return fail(FV_EINVAL, "gravity g must be finite and > 0");
+        if (!(p1 > -1e300 && p1 < 1e300)) return fail(FV_EINVAL, "Coriolis parameter f must be finite");
+    } else {
+        return fail(FV_EINVAL, "unknown PDE %d", pde);
+    }
     const int max_edge = dim == 2 ? kMaxEdge2D : kMaxEdge3D;
     for (int i = 0; i < num_patches; ++i)
         if (patch_size[i] < 1 || patch_size[i] > max_edge)
@@ -268,7 +279,8 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     probe.uniform_p = uni;
     probe.halo_mode = halo_mode;
     probe.align_bytes = align;
-    if (num_patches > 0 && fv::fused_supported(probe, precision, &fk)) build_work_list(b, order, b->items_h);
+    if (pde == FV_PDE_EULER && num_patches > 0 && fv::fused_supported(probe, precision, &fk))
+        build_work_list(b, order, b->items_h);
     b->fused_kernel = fk;
 
     // One device block: offsets, sizes, flags, work list, order, counter.
@@ -318,6 +330,9 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     v.max_p = max_p;
     v.uniform_p = uni;
     v.align_bytes = align;
+    v.pde = pde == FV_PDE_SHALLOW_WATER ? fv::PDE_SHALLOW_WATER : fv::PDE_EULER;
+    v.pde_param[0] = p0;
+    v.pde_param[1] = p1;
     b->plan.items = reinterpret_cast<const fv::WorkItem *>(m + off_items);
     b->plan.order = reinterpret_cast<const int32_t *>(m + off_order);
     b->plan.num_items = (int)b->items_h.size();
@@ -338,8 +353,17 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     b->plan.shape.blocks_per_sm = 0;
 
     // Default form: fused sweep if this build covers the shapes, else the
-    // patch-wise tile kernel, else the loop cascade.
-    if (fk != fv::FUSED_NONE) b->form = FV_FORM_FUSED;
+    // patch-wise tile kernel, else the loop cascade.  Other PDEs than Euler
+    // run on the generic patch-wise kernel only.
+    if (pde != FV_PDE_EULER) {
+        if (num_patches > 0 && !fv::pde_tile_supported(v, precision)) {
+            cudaStreamDestroy(b->capture_stream);
+            cudaFree(b->meta);
+            delete b;
+            return fail(FV_EUNSUPPORTED, "generic PDE kernel: patch too large for shared memory");
+        }
+        b->form = FV_FORM_TILE;
+    } else if (fk != fv::FUSED_NONE) b->form = FV_FORM_FUSED;
     else if (num_patches == 0 || fv::tile_supported(v, precision)) b->form = FV_FORM_TILE;
     else {
         b->form = FV_FORM_CASCADE;
@@ -355,10 +379,38 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
     return FV_OK;
 }
 
+int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *patch_size,
+                    int halo, int unknowns, int precision, int halo_mode, double gamma,
+                    void *cuda_stream)
+{
+    return create_batch(out, FV_PDE_EULER, dim, num_patches, patch_size, halo, unknowns, precision, halo_mode,
+                        gamma, 0.0, cuda_stream);
+}
+
+int fv_batch_create_pde(fv_batch_t **out, int pde, int dim, int num_patches, const int32_t *patch_size,
+                        int precision, int halo_mode, const double *params, int num_params, void *cuda_stream)
+{
+    g_last_error.clear();
+    if (out) *out = nullptr;
+    if (pde == FV_PDE_EULER) {
+        if (!params || num_params != 1) return fail(FV_EINVAL, "Euler takes one parameter (gamma)");
+        return create_batch(out, pde, dim, num_patches, patch_size, 1, dim + 2, precision, halo_mode, params[0],
+                            0.0, cuda_stream);
+    }
+    if (pde == FV_PDE_SHALLOW_WATER) {
+        if (!params || num_params != 2) return fail(FV_EINVAL, "shallow water takes two parameters (g, f)");
+        return create_batch(out, pde, dim, num_patches, patch_size, 1, 4, precision, halo_mode, params[0],
+                            params[1], cuda_stream);
+    }
+    return fail(FV_EINVAL, "unknown PDE %d", pde);
+}
+
 int fv_batch_set_form(fv_batch_t *b, int form)
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
+    if (b->view.pde != fv::PDE_EULER && form != FV_FORM_TILE)
+        return fail(FV_EUNSUPPORTED, "this PDE runs on the generic patch-wise kernel (FV_FORM_TILE) only");
     if (form == FV_FORM_CASCADE || form == FV_FORM_TASKGRAPH) {
         int rc = ensure_scratch(b);
         if (rc) return rc;
@@ -502,7 +554,10 @@ static int launch_update(fv_batch_t *b, cudaStream_t st, const void *Q_in, void 
         e = fv::launch_cascade_update(b->view, b->precision, a, b->cs, st, b->cascade_layout);
         break;
     case FV_FORM_TASKGRAPH: return launch_taskgraph(b, st, a);
-    case FV_FORM_TILE: e = fv::launch_tile_update(b->view, b->precision, a, st); break;
+    case FV_FORM_TILE:
+        e = b->view.pde == fv::PDE_EULER ? fv::launch_tile_update(b->view, b->precision, a, st)
+                                         : fv::launch_pde_update(b->view, b->precision, a, st);
+        break;
     default: e = fv::launch_fused_update(b->view, b->precision, a, b->plan, st); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "update launch");
@@ -539,7 +594,9 @@ int fv_max_eigenvalue(fv_batch_t *b, const void *Q, double *lambda_out)
     if (!Q || !lambda_out) return fail(FV_EINVAL, "NULL pointer");
     if (!aligned16(Q)) return fail(FV_EINVAL, "state buffer must be 16-byte aligned");
     DeviceGuard dg(b->device);
-    cudaError_t e = fv::launch_max_eigenvalue(b->view, b->precision, Q, lambda_out, b->stream);
+    cudaError_t e = b->view.pde == fv::PDE_EULER
+                        ? fv::launch_max_eigenvalue(b->view, b->precision, Q, lambda_out, b->stream)
+                        : fv::launch_pde_max_eigenvalue(b->view, b->precision, Q, lambda_out, b->stream);
     return e == cudaSuccess ? FV_OK : cuda_fail(e, "max eigenvalue launch");
 }
 
@@ -687,9 +744,10 @@ int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len)
                      : (b->fused_kernel == fv::FUSED_SWEEP3D ? fv::fused3d_kernel_name(b->view, b->precision)
                                                              : "none");
     snprintf(buf, len, "form=%s precision=%s dim=%d patches=%d max_p=%d uniform_p=%d fused_kernel=%s "
-             "items=%d warps_per_block=%d blocks_per_sm=%d scratch_bytes=%zu cascade_layout=%s",
+             "items=%d warps_per_block=%d blocks_per_sm=%d scratch_bytes=%zu cascade_layout=%s pde=%s",
              form, prec, b->dim, b->T, b->view.max_p, b->view.uniform_p, fk, b->plan.num_items,
-             b->plan.shape.warps_per_block, b->plan.shape.blocks_per_sm, b->scratch_bytes, lay);
+             b->plan.shape.warps_per_block, b->plan.shape.blocks_per_sm, b->scratch_bytes, lay,
+             b->view.pde == fv::PDE_EULER ? "euler" : "shallow_water");
     return FV_OK;
 }
 

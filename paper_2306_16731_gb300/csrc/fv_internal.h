@@ -26,7 +26,11 @@ struct BatchView {
     int align_bytes;           // largest power of two <= 16 dividing every patch's (and 3D plane's) bytes
     const int32_t *nbr;        // [T][2 dim] neighbour across -x,+x,-y,+y[,-z,+z] or -1; null = none registered
     int test_wait_expiry;      // test hook: bounded copy waits are made to run out (FV_ETIMEOUT)
+    int pde;                   // PDE_EULER or PDE_SHALLOW_WATER
+    double pde_param[2];       // shallow water: gravity g, Coriolis parameter f
 };
+
+enum PdeKind { PDE_EULER = 0, PDE_SHALLOW_WATER = 1 };
 
 // Arguments of one update.
 struct StepArgs {
@@ -108,6 +112,12 @@ bool fused3d_p8_applies(const BatchView &b, int precision, const void *q_in, con
 cudaError_t launch_fused3d_p8(const BatchView &b, int precision, const StepArgs &a, int first, int count,
                               const FusedShape &shape, cudaStream_t st);
 int fused_items_for(int dim, int p, int *patches_per_item);
+
+// Generic PDE of Eq. 1 on the patch-wise realisation (fv_pde.cu).
+bool pde_tile_supported(const BatchView &b, int precision);
+cudaError_t launch_pde_update(const BatchView &b, int precision, const StepArgs &a, cudaStream_t st);
+cudaError_t launch_pde_max_eigenvalue(const BatchView &b, int precision, const void *q, double *lambda_out,
+                                      cudaStream_t st);
 
 cudaError_t launch_halo_exchange(const BatchView &b, int precision, const int32_t *nbr, void *q,
                                  cudaStream_t st);

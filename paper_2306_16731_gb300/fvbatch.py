@@ -35,6 +35,8 @@ FV_FORM_FUSED = 0
 FV_FORM_CASCADE = 1
 FV_FORM_TILE = 2
 FV_FORM_TASKGRAPH = 3
+FV_PDE_EULER = 0
+FV_PDE_SHALLOW_WATER = 1
 FV_LAYOUT_AOS = 0
 FV_LAYOUT_SOA = 1
 FV_LAYOUT_AOSOA = 2
@@ -49,7 +51,7 @@ EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_ba
            "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
            "fv_batch_scratch_bytes", "fv_batch_describe", "fv_batch_launches_per_update",
-           "fv_batch_test_wait_expiry", "fv_batch_set_cascade_layout"]
+           "fv_batch_test_wait_expiry", "fv_batch_set_cascade_layout", "fv_batch_create_pde"]
 
 
 class FVError(RuntimeError):
@@ -83,6 +85,8 @@ def load() -> ctypes.CDLL:
         i, d = ctypes.c_int, ctypes.c_double
         sig = {
             "fv_batch_create": (i, [ctypes.POINTER(_vp), i, i, ctypes.POINTER(ctypes.c_int32), i, i, i, i, d, _vp]),
+            "fv_batch_create_pde": (i, [ctypes.POINTER(_vp), i, i, i, ctypes.POINTER(ctypes.c_int32), i, i,
+                                        ctypes.POINTER(ctypes.c_double), i, _vp]),
             "fv_batch_set_form": (i, [_vp, i]),
             "fv_batch_set_stream": (i, [_vp, _vp]),
             "fv_batch_set_launch_shape": (i, [_vp, i, i]),
@@ -169,6 +173,19 @@ def fv_batch_set_launch_shape(b, warps_per_block, blocks_per_sm):
     return _check(load().fv_batch_set_launch_shape(b, int(warps_per_block), int(blocks_per_sm)))
 
 
+def fv_batch_create_pde(pde, dim, patch_size, precision, halo_mode, params, stream=0):
+    """Batch for one of the FV_PDE_* systems; ``params`` are host floats."""
+    lib = load()
+    ps = [int(v) for v in patch_size]
+    arr = (ctypes.c_int32 * max(1, len(ps)))(*ps) if ps else None
+    pv = [float(v) for v in params]
+    parr = (ctypes.c_double * max(1, len(pv)))(*pv)
+    h = _vp()
+    _check(lib.fv_batch_create_pde(ctypes.byref(h), int(pde), int(dim), len(ps), arr, int(precision),
+                                   int(halo_mode), parr, len(pv), _vp(stream or 0)))
+    return h.value
+
+
 def fv_batch_set_cascade_layout(b, layout):
     return _check(load().fv_batch_set_cascade_layout(b, int(layout)))
 
@@ -252,7 +269,7 @@ class FVBatch:
     """Owns one batch handle; methods forward to the C entry points."""
 
     def __init__(self, dim, patch_size, precision=FV_F64, halo_mode=FV_HALO_FIXED,
-                 gamma=1.4, stream=None, form=None):
+                 gamma=1.4, stream=None, form=None, pde=FV_PDE_EULER, params=None):
         import torch
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
@@ -260,7 +277,12 @@ class FVBatch:
         self.patch_size = [int(v) for v in patch_size]
         self.precision = int(precision)
         self.halo_mode = int(halo_mode)
-        self.handle = fv_batch_create(dim, self.patch_size, 1, dim + 2, precision, halo_mode, gamma, stream)
+        self.pde = int(pde)
+        if self.pde == FV_PDE_EULER and params is None:
+            self.handle = fv_batch_create(dim, self.patch_size, 1, dim + 2, precision, halo_mode, gamma, stream)
+        else:
+            self.handle = fv_batch_create_pde(self.pde, dim, self.patch_size, precision, halo_mode,
+                                              params if params is not None else [gamma], stream)
         if form is not None:
             fv_batch_set_form(self.handle, form)
 

@@ -175,6 +175,25 @@ def uniform_batch(dim: int, patch_size, seed: int, dx=0.1, dtype=np.float64,
                     halo_mode=halo_mode, steps=steps, Q0=Q.reshape(-1), seed=seed)
 
 
+def shallow_water_batch(patch_size, seed: int, dx=0.1, dtype=np.float64, halo_mode: int = FIXED,
+                        bottom: float = 0.2, depth_noise: float = 0.05, speed: float = 0.3) -> Workload:
+    """2D shallow water batch, Q = (h, hu, hv, b) per volume (halo volumes
+    included): a perturbed lake over a random bottom, b ~ U[-bottom, bottom],
+    h = 1 - b + U[-depth_noise, depth_noise], u, v ~ U[-speed, speed]."""
+    psz = np.asarray(patch_size, dtype=np.int32).reshape(-1)
+    T = len(psz)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ncells = int(np.sum((psz.astype(np.int64) + 2) ** 2))
+    b = rng.uniform(-bottom, bottom, ncells)
+    h = 1.0 - b + rng.uniform(-depth_noise, depth_noise, ncells)
+    u = rng.uniform(-speed, speed, ncells)
+    v = rng.uniform(-speed, speed, ncells)
+    Q = np.stack([h, h * u, h * v, b], axis=1).astype(dtype)
+    dxa = np.broadcast_to(np.asarray(dx, dtype=np.float64), (T,)).copy()
+    return Workload(name="shallow_water_2d", dim=2, patch_size=psz, dx=dxa, halo_mode=halo_mode,
+                    steps=1, Q0=Q.reshape(-1), seed=seed)
+
+
 def patch_view(w: Workload, Q: np.ndarray, i: int) -> np.ndarray:
     """Patch ``i`` of a flat state as an array [(p+2)]*d + [d+2] (z, y, x, k)."""
     off = w.offsets()

@@ -673,3 +673,117 @@ def test_taskgraph_form_multi_step_run_equals_cascade():
     a = gpu_run(w, 0, FORMS["cascade"], 5)
     b = gpu_run(w, 0, 3, 5, use_graph=True)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+# ------------------------------------------------- generic PDE (Eq. 1): shallow water
+
+SWE_G, SWE_F = 9.81, 0.6
+
+
+def _swe_batch(w, precision, form=None):
+    from paper_2306_16731_gb300 import fvbatch as fb
+    return fb.FVBatch(2, w.patch_size, precision=precision, halo_mode=w.halo_mode, form=form,
+                      pde=fb.FV_PDE_SHALLOW_WATER, params=[SWE_G, SWE_F])
+
+
+@pytest.mark.parametrize("halo", [inputs.FIXED, inputs.PERIODIC])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_shallow_water_step_matches_oracle(halo, precision):
+    """One step of the generic-PDE kernel (Rusanov flux, averaged
+    non-conservative product, Coriolis source) against the oracle, with the
+    eigenvalues and CFL time steps of the new state."""
+    import torch
+    w = inputs.shallow_water_batch([3, 8, 16, 5, 32, 1, 12] * 3, seed=131 + halo, dx=np.linspace(0.02, 0.1, 21),
+                                   halo_mode=halo)
+    T = w.num_patches
+    b = _swe_batch(w, precision)
+    assert "pde=shallow_water" in b.describe() and "form=tile" in b.describe()
+    q0 = initial_fp64(w.Q0, precision)
+    lam0 = oracle.swe_batch_max_eigenvalue(w.patch_size, q0, SWE_G)
+    dt = 0.4 * w.dx / (2 * lam0)
+    qa = to_device(w.Q0, precision)
+    qb = qa.clone()
+    dx = torch.tensor(w.dx, device="cuda")
+    dtv = torch.tensor(dt, device="cuda")
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dtn = torch.zeros_like(lam)
+    lg = torch.zeros_like(lam)
+    b.max_eigenvalue(qa, lg)
+    b.update(qa, qb, dx, dtv, lam, dtn, 0.4)
+    b.status()
+    ref, lref = oracle.swe_batch_step(w.patch_size, w.dx, dt, q0, SWE_G, SWE_F, halo)
+    got = qb.to(torch.float64).cpu().numpy()
+    tol = 1e-12 if precision == 0 else 1e-5
+    assert batch_rel_linf(got, ref, 2, w.patch_size) < tol
+    assert np.max(np.abs(lg.cpu().numpy() - lam0) / lam0) < tol
+    assert np.max(np.abs(lam.cpu().numpy() - lref) / lref) < tol
+    assert np.allclose(dtn.cpu().numpy(), 0.4 * w.dx / (2 * lam.cpu().numpy()), rtol=1e-15, atol=0)
+    # the bathymetry is a parameter: copied bitwise
+    for g_, q_ in zip(patches_interior(got, 2, w.patch_size), patches_interior(q0, 2, w.patch_size)):
+        assert np.array_equal(g_[..., 3], q_[..., 3])
+    b.close()
+
+
+def test_shallow_water_cfl_chained_run_and_graph_replay():
+    """Ten CFL-chained steps on the GPU (eager and as one CUDA graph, bitwise
+    equal) against the oracle chained the same way."""
+    w = inputs.shallow_water_batch([16] * 30 + [7] * 11, seed=141, dx=0.05)
+    steps = 10
+    from paper_2306_16731_gb300 import fvbatch as fb
+    res = []
+    for use_graph in (False, True):
+        import torch
+        b = _swe_batch(w, 0)
+        qa = to_device(w.Q0, 0)
+        qb = qa.clone()
+        dx = torch.tensor(w.dx, device="cuda")
+        lam = torch.zeros(w.num_patches, dtype=torch.float64, device="cuda")
+        dta, dtb = torch.zeros_like(lam), torch.zeros_like(lam)
+        b.max_eigenvalue(qa, lam)
+        b.cfl_time_step(lam, dx, 0.4, dta)
+        b.run(qa, qb, dx, dta, dtb, lam, steps, 0.4, use_graph)
+        b.status()
+        res.append(((qb if steps % 2 else qa).cpu().numpy(), lam.cpu().numpy()))
+        b.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    q = w.Q0.astype(np.float64)
+    lamo = oracle.swe_batch_max_eigenvalue(w.patch_size, q, SWE_G)
+    for _ in range(steps):
+        dt = 0.4 * w.dx / (2 * lamo)
+        q, lamo = oracle.swe_batch_step(w.patch_size, w.dx, dt, q, SWE_G, SWE_F, w.halo_mode)
+    assert batch_rel_linf(res[0][0], q, 2, w.patch_size) < 1e-12
+
+
+def test_shallow_water_lake_at_rest_keeps_zero_momentum_on_gpu():
+    import torch
+    w = inputs.shallow_water_batch([16] * 8, seed=151, dx=0.1, depth_noise=0.0, speed=0.0, bottom=0.5)
+    b = _swe_batch(w, 0)
+    qa = to_device(w.Q0, 0)
+    qb = qa.clone()
+    dx = torch.tensor(w.dx, device="cuda")
+    dt = torch.full((8,), 0.004, dtype=torch.float64, device="cuda")
+    b.update(qa, qb, dx, dt, None, None, 0.4)
+    b.status()
+    got = qb.cpu().numpy().reshape(-1, 4)
+    scale = 0.004 / 0.1 * 0.5 * SWE_G * np.max(w.Q0.reshape(-1, 4)[:, 0]) ** 2
+    assert np.max(np.abs(got[:, 1:3])) <= 1e-13 * scale
+    b.close()
+
+
+def test_shallow_water_rejects_what_it_does_not_cover():
+    from paper_2306_16731_gb300 import fvbatch as fb
+    with pytest.raises(fb.FVError) as e:
+        fb.FVBatch(3, [4], pde=fb.FV_PDE_SHALLOW_WATER, params=[9.81, 0.0])
+    assert e.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as e:
+        fb.FVBatch(2, [4], precision=fb.FV_BF16_F32, pde=fb.FV_PDE_SHALLOW_WATER, params=[9.81, 0.0])
+    assert e.value.code == fb.FV_EUNSUPPORTED
+    with pytest.raises(fb.FVError) as e:
+        fb.FVBatch(2, [4], pde=fb.FV_PDE_SHALLOW_WATER, params=[-1.0, 0.0])
+    assert e.value.code == fb.FV_EINVAL
+    b = fb.FVBatch(2, [4, 8], pde=fb.FV_PDE_SHALLOW_WATER, params=[9.81, 0.0])
+    for form in (fb.FV_FORM_FUSED, fb.FV_FORM_CASCADE, fb.FV_FORM_TASKGRAPH):
+        with pytest.raises(fb.FVError) as e:
+            b.set_form(form)
+        assert e.value.code == fb.FV_EUNSUPPORTED
+    b.close()

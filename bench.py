@@ -377,6 +377,11 @@ def run_ours(args):
     barrier()
     e2e["direct_mapped_value"] = whole_job_rate(vols * ke, time.perf_counter() - t_d, dist, dev)
 
+    # patches as separate host objects (the paper's heap patches): one pinned
+    # arena per side with the patches in shuffled order and random gaps;
+    # gather/scatter kernels over the coherent link vs one copy per patch
+    e2e["scattered_patches"] = scattered_e2e(b32, w, host_dx, host_dt, host_lam, dist, dev)
+
     if not args.no_other_workloads and world == 1:
         forms_other = other_workloads(dev, stream, flush_l2, args.steps)
         abl = ablations(dev, stream, flush_l2)
@@ -444,6 +449,43 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return out
+
+
+def scattered_e2e(b, w, host_dx, host_dt, host_lam, dist, dev, k=5):
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    from paper_2306_16731_gb300.multigpu import whole_job_rate
+    T = w.num_patches
+    off = w.offsets()
+    sizes = np.diff(off) * 4                           # FP32 bytes per patch
+    rng = np.random.default_rng(17)
+    gaps = rng.integers(0, 256, T) * 16                # up to 4 KB between patches
+    order = rng.permutation(T)
+    pos = np.zeros(T, dtype=np.int64)
+    cur = 0
+    for i in order:
+        cur += int(gaps[i])
+        pos[i] = cur
+        cur += int(sizes[i] + 15) // 16 * 16
+    arena_in = torch.empty(cur, dtype=torch.uint8).pin_memory()
+    arena_out = torch.empty(cur, dtype=torch.uint8).pin_memory()
+    src = np.frombuffer(w.Q0.astype(np.float32).tobytes(), dtype=np.uint8)
+    a_in = arena_in.numpy()
+    for i in range(T):
+        a_in[pos[i]:pos[i] + sizes[i]] = src[off[i] * 4:off[i + 1] * 4]
+    base_in, base_out = arena_in.data_ptr(), arena_out.data_ptr()
+    b.set_host_patches([base_in + int(x) for x in pos], [base_out + int(x) for x in pos])
+    res = {"patches": T, "arena_bytes": int(cur), "layout": "shuffled order, 0-4 KB gaps, one pinned arena per side"}
+    for name, flags, steps in (("gather_kernels", 0, k), ("per_patch_copies", fb.FV_SCATTER_COPIES, 2)):
+        b.update_scattered(host_dx, host_dt, host_lam, None, w.cfl, flags)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s_ in range(steps):
+            b.update_scattered(host_dx, host_dt, host_lam, None, w.cfl, flags | (fb.FV_SCATTER_SWAP if s_ & 1 else 0))
+        el = time.perf_counter() - t0
+        res[name] = {"value": whole_job_rate(w.interior_volumes * steps, el, dist, dev), "ms_per_step": el / steps * 1e3}
+    b.set_host_patches(None, None)
+    return res
 
 
 def ablations(dev, stream, flush_l2, k=5):

@@ -182,6 +182,36 @@ int fv_batch_set_neighbours(fv_batch_t *b, const int32_t *neighbours);
  * batch's stream.  FV_EINVAL without a registered table. */
 int fv_halo_exchange(fv_batch_t *b, void *Q);
 
+/*
+ * Patches kept as separate host allocations, as in the paper's framework
+ * (each patch a heap object; moving them dominates its run time, Sec. 4
+ * "Data transfer", Sec. 5 Fig. 4).  patch_in[i] and patch_out[i] (HOST
+ * arrays of num_patches pointers) each address one halo-inclusive patch in
+ * the batch layout of a single patch (N (p_i+2)^d values of the storage
+ * type), in page-locked host memory (cudaHostAlloc or cudaHostRegister;
+ * anything else gives FV_EINVAL).  The caller keeps every buffer alive and
+ * at least that large while registered.  Pointers are validated and
+ * translated once and their device table is uploaded (allocates once,
+ * FV_ENOMEM); both NULL clears the registration.
+ */
+int fv_batch_set_host_patches(fv_batch_t *b, const void *const *patch_in, void *const *patch_out);
+
+/*
+ * One update of the registered host patches: gather them into the batch's
+ * device staging (the buffers of fv_patch_batch_update_host), update,
+ * write each patch's interior volumes back (halo volumes of the output
+ * patches are not written), with dx/dt/lambda/dt_next as HOST arrays as in
+ * fv_patch_batch_update_host.  flags: FV_SCATTER_SWAP reads the output
+ * patches and writes the input patches (ping-pong); FV_SCATTER_COPIES moves
+ * the patches with one cudaMemcpyAsync per patch in and pitched copies of the
+ * interior rows out instead of the gather and scatter kernels (which read and
+ * write the page-locked memory over the coherent CPU-GPU link, one block per
+ * patch).  Synchronous.
+ */
+enum { FV_SCATTER_SWAP = 1, FV_SCATTER_COPIES = 2 };
+int fv_patch_batch_update_scattered(fv_batch_t *b, const double *dx_host, const double *dt_host,
+                                    double *lambda_host, double *dt_next_host, double cfl, int flags);
+
 /* Rebind the batch to another stream (e.g. a capture stream). */
 int fv_batch_set_stream(fv_batch_t *b, void *cuda_stream);
 

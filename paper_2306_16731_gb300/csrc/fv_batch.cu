@@ -95,6 +95,11 @@ struct fv_batch {
     double *hs_arrays = nullptr;       // dx, dt, lambda, dt_next (T each)
     cudaStream_t hs_copy_in = nullptr, hs_copy_out = nullptr;
     std::vector<cudaEvent_t> hs_events;
+
+    // scattered host patches (fv_batch_set_host_patches): device table of
+    // device-visible addresses [in T | out T] and the host addresses
+    void **sp_table = nullptr;
+    std::vector<void *> sp_in, sp_out;
 };
 
 namespace fv {
@@ -710,6 +715,7 @@ int fv_batch_destroy(fv_batch_t *b)
     if (b->hs_in) cudaFree(b->hs_in);
     if (b->hs_out) cudaFree(b->hs_out);
     if (b->hs_arrays) cudaFree(b->hs_arrays);
+    if (b->sp_table) cudaFree(b->sp_table);
     if (b->hs_copy_in) cudaStreamDestroy(b->hs_copy_in);
     if (b->hs_copy_out) cudaStreamDestroy(b->hs_copy_out);
     for (cudaEvent_t e : b->hs_events) cudaEventDestroy(e);
@@ -1042,4 +1048,112 @@ done:
         save_tune_file();
     }
     return FV_OK;
+}
+
+// ------------------------------------------------ scattered host patches
+
+extern "C" int fv_batch_set_host_patches(fv_batch_t *b, const void *const *patch_in, void *const *patch_out)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    DeviceGuard dg(b->device);
+    if (!patch_in && !patch_out) {
+        b->sp_in.clear();
+        b->sp_out.clear();
+        return FV_OK;
+    }
+    if (!patch_in || !patch_out) return fail(FV_EINVAL, "both patch tables are needed (or both NULL)");
+    std::vector<void *> dev(2 * (size_t)b->T);
+    for (int side = 0; side < 2; ++side)
+        for (int i = 0; i < b->T; ++i) {
+            const void *ptr = side == 0 ? patch_in[i] : patch_out[i];
+            if (!ptr) return fail(FV_EINVAL, "patch %d: NULL %s pointer", i, side ? "output" : "input");
+            cudaPointerAttributes at;
+            cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+            if (e != cudaSuccess || at.type != cudaMemoryTypeHost || !at.devicePointer) {
+                cudaGetLastError();
+                return fail(FV_EINVAL, "patch %d: %s is not page-locked host memory (cudaHostAlloc/cudaHostRegister)",
+                            i, side ? "output" : "input");
+            }
+            dev[side * (size_t)b->T + i] = at.devicePointer;
+        }
+    for (int i = 0; i < b->T; ++i)
+        if (patch_in[i] == patch_out[i]) return fail(FV_EINVAL, "patch %d: input and output alias", i);
+    if (!b->sp_table && b->T > 0) {
+        cudaError_t e = cudaMalloc((void **)&b->sp_table, 2 * (size_t)b->T * sizeof(void *));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FV_ENOMEM, "patch address table");
+        }
+    }
+    if (b->T > 0) {
+        cudaError_t e = cudaMemcpy(b->sp_table, dev.data(), dev.size() * sizeof(void *), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "patch address table upload");
+    }
+    b->sp_in.resize(b->T);
+    b->sp_out.resize(b->T);
+    for (int i = 0; i < b->T; ++i) {
+        b->sp_in[i] = const_cast<void *>(patch_in[i]);
+        b->sp_out[i] = patch_out[i];
+    }
+    return FV_OK;
+}
+
+extern "C" int fv_patch_batch_update_scattered(fv_batch_t *b, const double *dx_host, const double *dt_host,
+                                               double *lambda_host, double *dt_next_host, double cfl, int flags)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (b->T == 0) return FV_OK;
+    if ((int)b->sp_in.size() != b->T) return fail(FV_EINVAL, "no host patches registered (fv_batch_set_host_patches)");
+    if (!dx_host || !dt_host) return fail(FV_EINVAL, "NULL host pointer");
+    if (dt_next_host && !(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
+    if (flags & ~(FV_SCATTER_SWAP | FV_SCATTER_COPIES)) return fail(FV_EINVAL, "unknown flags 0x%x", flags);
+    DeviceGuard dg(b->device);
+    int rc = host_staging(b);
+    if (rc) return rc;
+    const bool swap = flags & FV_SCATTER_SWAP, copies = flags & FV_SCATTER_COPIES;
+    const size_t es = elem_bytes(b->precision);
+    const int T = b->T;
+    double *ddx = b->hs_arrays, *ddt = ddx + T, *dl = ddt + T, *dn = dl + T;
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaMemcpyAsync(ddx, dx_host, (size_t)T * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ddt, dt_host, (size_t)T * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "dx/dt upload");
+    unsigned char *qi = static_cast<unsigned char *>(b->hs_in), *qo = static_cast<unsigned char *>(b->hs_out);
+    const std::vector<void *> &src = swap ? b->sp_out : b->sp_in;
+    const std::vector<void *> &dst = swap ? b->sp_in : b->sp_out;
+    void **src_tab = b->sp_table + (swap ? T : 0), **dst_tab = b->sp_table + (swap ? 0 : T);
+    if (copies) {
+        // the paper's explicit transfers: one copy per patch
+        for (int i = 0; i < T && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(qi + b->elem_off[i] * es, src[i], (size_t)(b->elem_off[i + 1] - b->elem_off[i]) * es,
+                                cudaMemcpyHostToDevice, st);
+    } else {
+        e = fv::launch_gather_patches(b->view, src_tab, qi, (int)es, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "patch gather");
+    rc = launch_update(b, st, qi, qo, ddx, ddt, lambda_host ? dl : nullptr, dt_next_host ? dn : nullptr, cfl);
+    if (rc) return rc;
+    if (copies) {
+        // interior rows back: one pitched copy per 2D patch, per z-plane in 3D
+        const int N = b->dim + 2;
+        for (int i = 0; i < T && e == cudaSuccess; ++i) {
+            const int p = b->psize[i];
+            const size_t e1 = (size_t)p + 2, pitch = e1 * N * es, width = (size_t)p * N * es;
+            const int planes = b->dim == 2 ? 1 : p;
+            for (int z = 0; z < planes && e == cudaSuccess; ++z) {
+                const size_t first = (b->dim == 2 ? e1 + 1 : ((size_t)(z + 1) * e1 + 1) * e1 + 1) * N * es;
+                e = cudaMemcpy2DAsync(static_cast<unsigned char *>(dst[i]) + first, pitch,
+                                      qo + b->elem_off[i] * es + first, pitch, width, (size_t)p,
+                                      cudaMemcpyDeviceToHost, st);
+            }
+        }
+    } else {
+        e = fv::launch_scatter_interiors(b->view, qo, dst_tab, (int)es, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "patch scatter");
+    if (lambda_host) e = cudaMemcpyAsync(lambda_host, dl, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && dt_next_host)
+        e = cudaMemcpyAsync(dt_next_host, dn, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "scattered update");
 }

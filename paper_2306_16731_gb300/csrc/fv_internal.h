@@ -113,6 +113,12 @@ cudaError_t launch_fused3d_p8(const BatchView &b, int precision, const StepArgs 
                               const FusedShape &shape, cudaStream_t st);
 int fused_items_for(int dim, int p, int *patches_per_item);
 
+// Patches held as separate host allocations (fv_scatter.cu): gather into the
+// batch layout, scatter the updated interiors back; src/dst are device
+// tables of device-visible host addresses.
+cudaError_t launch_gather_patches(const BatchView &b, const void *const *src, void *dst, int es, cudaStream_t st);
+cudaError_t launch_scatter_interiors(const BatchView &b, const void *src, void *const *dst, int es, cudaStream_t st);
+
 // Generic PDE of Eq. 1 on the patch-wise realisation (fv_pde.cu).
 bool pde_tile_supported(const BatchView &b, int precision);
 cudaError_t launch_pde_update(const BatchView &b, int precision, const StepArgs &a, cudaStream_t st);

@@ -40,6 +40,8 @@ FV_PDE_SHALLOW_WATER = 1
 FV_LAYOUT_AOS = 0
 FV_LAYOUT_SOA = 1
 FV_LAYOUT_AOSOA = 2
+FV_SCATTER_SWAP = 1
+FV_SCATTER_COPIES = 2
 
 _ERRNAMES = {FV_EINVAL: "FV_EINVAL", FV_ENOMEM: "FV_ENOMEM", FV_ECUDA: "FV_ECUDA",
              FV_EUNSUPPORTED: "FV_EUNSUPPORTED", FV_ENONPHYSICAL: "FV_ENONPHYSICAL",
@@ -51,7 +53,8 @@ EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_ba
            "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
            "fv_batch_scratch_bytes", "fv_batch_describe", "fv_batch_launches_per_update",
-           "fv_batch_test_wait_expiry", "fv_batch_set_cascade_layout", "fv_batch_create_pde"]
+           "fv_batch_test_wait_expiry", "fv_batch_set_cascade_layout", "fv_batch_create_pde",
+           "fv_batch_set_host_patches", "fv_patch_batch_update_scattered"]
 
 
 class FVError(RuntimeError):
@@ -92,6 +95,8 @@ def load() -> ctypes.CDLL:
             "fv_batch_set_launch_shape": (i, [_vp, i, i]),
             "fv_batch_test_wait_expiry": (i, [_vp, i]),
             "fv_batch_set_cascade_layout": (i, [_vp, i]),
+            "fv_batch_set_host_patches": (i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+            "fv_patch_batch_update_scattered": (i, [_vp, _vp, _vp, _vp, _vp, d, i]),
             "fv_batch_set_neighbours": (i, [_vp, ctypes.POINTER(ctypes.c_int32)]),
             "fv_patch_batch_update_host": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, d, i]),
             "fv_halo_exchange": (i, [_vp, _vp]),
@@ -184,6 +189,23 @@ def fv_batch_create_pde(pde, dim, patch_size, precision, halo_mode, params, stre
     _check(lib.fv_batch_create_pde(ctypes.byref(h), int(pde), int(dim), len(ps), arr, int(precision),
                                    int(halo_mode), parr, len(pv), _vp(stream or 0)))
     return h.value
+
+
+def fv_batch_set_host_patches(b, patch_in, patch_out):
+    """patch_in / patch_out: sequences of host addresses (ints or pinned CPU
+    tensors), one per patch, or both None to clear."""
+    if patch_in is None and patch_out is None:
+        return _check(load().fv_batch_set_host_patches(b, None, None))
+    ai = [_addr(x) for x in patch_in]
+    ao = [_addr(x) for x in patch_out]
+    ti = (_vp * max(1, len(ai)))(*ai)
+    to = (_vp * max(1, len(ao)))(*ao)
+    return _check(load().fv_batch_set_host_patches(b, ti, to))
+
+
+def fv_patch_batch_update_scattered(b, dx_host, dt_host, lambda_host=None, dt_next_host=None, cfl=0.4, flags=0):
+    return _check(load().fv_patch_batch_update_scattered(b, _addr(dx_host), _addr(dt_host), _addr(lambda_host),
+                                                         _addr(dt_next_host), float(cfl), int(flags)))
 
 
 def fv_batch_set_cascade_layout(b, layout):
@@ -305,6 +327,13 @@ class FVBatch:
 
     def set_launch_shape(self, warps_per_block, blocks_per_sm):
         fv_batch_set_launch_shape(self.handle, warps_per_block, blocks_per_sm)
+
+    def set_host_patches(self, patch_in, patch_out):
+        """Register per-patch page-locked host buffers (see fv_batch_set_host_patches)."""
+        fv_batch_set_host_patches(self.handle, patch_in, patch_out)
+
+    def update_scattered(self, dx_host, dt_host, lambda_host=None, dt_next_host=None, cfl=0.4, flags=0):
+        fv_patch_batch_update_scattered(self.handle, dx_host, dt_host, lambda_host, dt_next_host, cfl, flags)
 
     def set_cascade_layout(self, layout):
         """Layout of the cascade's (and task graph's) vector temporaries (FV_LAYOUT_*)."""

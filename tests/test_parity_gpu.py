@@ -787,3 +787,105 @@ def test_shallow_water_rejects_what_it_does_not_cover():
             b.set_form(form)
         assert e.value.code == fb.FV_EUNSUPPORTED
     b.close()
+
+
+# ------------------------------------------------- patches as separate host allocations
+
+def _host_patches(w, precision, fill=None):
+    """One page-locked allocation per patch (the input state, or a sentinel)."""
+    import torch
+    dt = torch_dtype(precision)
+    off = w.offsets()
+    out = []
+    for i in range(w.num_patches):
+        n = int(off[i + 1] - off[i])
+        t = torch.empty(n, dtype=dt, pin_memory=True)
+        if fill is None:
+            t.copy_(torch.from_numpy(np.asarray(w.Q0[off[i]:off[i + 1]], dtype=np.float64)).to(dt))
+        else:
+            t.fill_(fill)
+        out.append(t)
+    return out
+
+
+@pytest.mark.parametrize("dim,sizes,precision,halo", [(2, [16] * 60 + [8] * 20 + [5, 3, 32], 1, inputs.FIXED),
+                                                      (2, [16] * 40, 0, inputs.PERIODIC),
+                                                      (3, [8] * 30, 1, inputs.PERIODIC),
+                                                      (3, [6, 4, 8, 5] * 4, 0, inputs.FIXED)])
+@pytest.mark.parametrize("flags", [0, 2])
+def test_scattered_host_patches_match_the_device_update(dim, sizes, precision, halo, flags):
+    """Patches held as separate page-locked host allocations, gathered by a
+    kernel (flags 0) or copied one by one (flags 2), updated and their
+    interiors written back: bitwise the device update of the same batch, two
+    ping-pong steps; output halos are not written."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(dim, sizes, seed=161 + dim, dx=0.04, halo_mode=halo)
+    T = w.num_patches
+    ins = _host_patches(w, precision)
+    outs = _host_patches(w, precision, fill=-7.0)
+    b = fb.FVBatch(dim, w.patch_size, precision=precision, halo_mode=halo)
+    b.set_host_patches(ins, outs)
+    dx = torch.tensor(w.dx).pin_memory()
+    dt = torch.full((T,), 1e-3, dtype=torch.float64).pin_memory()
+    lam = torch.zeros(T, dtype=torch.float64).pin_memory()
+    dtn = torch.zeros_like(lam).pin_memory()
+    b.update_scattered(dx, dt, lam, dtn, 0.4, flags)
+    # reference: the device update of the contiguous batch
+    qa = to_device(w.Q0, precision)
+    qb = qa.clone()
+    ddx, ddt = dx.cuda(), dt.cuda()
+    rl, rn = torch.zeros(T, dtype=torch.float64, device="cuda"), torch.zeros(T, dtype=torch.float64, device="cuda")
+    b.update(qa, qb, ddx, ddt, rl, rn, 0.4)
+    b.status()
+    ref = qb.to(torch.float64).cpu().numpy()
+    got = np.concatenate([t.to(torch.float64).numpy() for t in outs])
+    gi, ri = patches_interior(got, dim, w.patch_size), patches_interior(ref, dim, w.patch_size)
+    for g_, r_ in zip(gi, ri):
+        assert np.array_equal(g_, r_)
+    assert np.array_equal(lam.numpy(), rl.cpu().numpy()) and np.array_equal(dtn.numpy(), rn.cpu().numpy())
+    # halo volumes of the output patches keep the sentinel
+    for t, p in zip(outs, w.patch_size):
+        shape = (int(p) + 2,) * dim + (dim + 2,)
+        a = t.to(torch.float64).numpy().reshape(shape)
+        mask = np.ones(shape[:-1], bool)
+        mask[(slice(1, -1),) * dim] = False
+        assert np.all(a[mask] == -7.0)
+    # second step the other way round (outputs read, inputs written); fixed
+    # halos are held in both ping-pong buffers, so the output patches get the
+    # input patches' halo volumes first
+    for t_in, t_out, p in zip(ins, outs, w.patch_size):
+        shape = (int(p) + 2,) * dim + (dim + 2,)
+        mask = np.ones(shape[:-1], bool)
+        mask[(slice(1, -1),) * dim] = False
+        t_out.numpy().reshape(shape)[mask] = t_in.numpy().reshape(shape)[mask]
+    b.update_scattered(dx, dt, lam, dtn, 0.4, flags | fb.FV_SCATTER_SWAP)
+    qa2 = qa.clone()
+    b.update(qb, qa2, ddx, ddt, rl, rn, 0.4)
+    b.status()
+    got2 = np.concatenate([t.to(torch.float64).numpy() for t in ins])
+    for g_, r_ in zip(patches_interior(got2, dim, w.patch_size),
+                      patches_interior(qa2.to(torch.float64).cpu().numpy(), dim, w.patch_size)):
+        assert np.array_equal(g_, r_)
+    b.set_host_patches(None, None)
+    b.close()
+
+
+def test_scattered_registration_rejects_pageable_memory():
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(2, [4, 4], seed=171)
+    b = fb.FVBatch(2, w.patch_size)
+    pageable = [np.zeros(144), np.zeros(144)]
+    pinned = _host_patches(w, 0)
+    with pytest.raises(fb.FVError) as e:
+        b.set_host_patches([a.ctypes.data for a in pageable], pinned)
+    assert e.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as e:
+        b.set_host_patches(pinned, pinned)             # aliasing
+    assert e.value.code == fb.FV_EINVAL
+    dx = torch.full((2,), 0.1, dtype=torch.float64).pin_memory()
+    with pytest.raises(fb.FVError) as e:
+        b.update_scattered(dx, dx)                      # nothing registered
+    assert e.value.code == fb.FV_EINVAL
+    b.close()

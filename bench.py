@@ -36,7 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "volume updates/s per GB300 (2D Euler Rusanov FV step, fused FP32 vs plain FP64 cascade)"
+METRIC = "volume updates/s per GB300, fused FP32 vs plain FP64 at stated error; % roofline"
 UNIT = "volume updates/s"
 WORKLOAD = "2D Euler, 16384 patches of 16x16 + 1-cell fixed halo, dx=0.01, CFL 0.4, seeded uniform primitives"
 

@@ -757,8 +757,7 @@ cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepA
         const bool blocks8 = precision != PREC_F64 && sp.p % 8 == 0 && sp.p <= 32 &&
                              smem3b_bytes(sp.p, precision) <= 227 * 1024;
         if (blocks8) {
-            if (precision == PREC_F64) e = launch3b<double>(sp, chunk, st, precision);
-            else if (precision == PREC_F32) e = launch3b<float>(sp, chunk, st, precision);
+            if (precision == PREC_F32) e = launch3b<float>(sp, chunk, st, precision);
             else e = launch3b<__nv_bfloat16>(sp, chunk, st, precision);
         } else if (precision == PREC_F64) e = launch3<double>(sp, chunk, st, precision);
         else if (precision == PREC_F32) e = launch3<float>(sp, chunk, st, precision);

@@ -889,3 +889,68 @@ def test_scattered_registration_rejects_pageable_memory():
         b.update_scattered(dx, dx)                      # nothing registered
     assert e.value.code == fb.FV_EINVAL
     b.close()
+
+
+def test_new_entry_points_handle_empty_batches_and_bad_arguments():
+    """Empty batches go through the task-graph form, the scattered host
+    patches and the generic PDE without work; invalid layouts, flags and
+    forms are refused."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    z = torch.zeros(1, dtype=torch.float64, device="cuda")
+    b = fb.FVBatch(2, [], form=3)
+    b.set_cascade_layout(fb.FV_LAYOUT_SOA)
+    b.update(z, torch.zeros_like(z), z, z, z, z, 0.4)
+    b.set_host_patches([], [])
+    hz = torch.zeros(1, dtype=torch.float64).pin_memory()
+    b.update_scattered(hz, hz)
+    b.status()
+    with pytest.raises(fb.FVError) as e:
+        b.set_cascade_layout(3)
+    assert e.value.code == fb.FV_EINVAL
+    b.close()
+    s = fb.FVBatch(2, [], pde=fb.FV_PDE_SHALLOW_WATER, params=[9.81, 0.1])
+    s.update(z, torch.zeros_like(z), z, z, z, z, 0.4)
+    s.status()
+    s.close()
+    w = inputs.uniform_batch(2, [4, 4], seed=181)
+    b = fb.FVBatch(2, w.patch_size)
+    ins = _host_patches(w, 0)
+    outs = _host_patches(w, 0, fill=0.0)
+    b.set_host_patches(ins, outs)
+    dx = torch.full((2,), 0.1, dtype=torch.float64).pin_memory()
+    with pytest.raises(fb.FVError) as e:
+        b.update_scattered(dx, dx, None, None, 0.4, 4)            # unknown flag
+    assert e.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as e:
+        fb.FVBatch(2, [4], pde=7, params=[1.0])
+    assert e.value.code == fb.FV_EINVAL
+    b.close()
+
+
+@pytest.mark.parametrize("chunks", [0, 3])
+def test_shallow_water_host_state_update_matches_device_update(chunks):
+    """The host-state update (pipelined copies, or kernels on the mapped host
+    buffers) drives the generic-PDE kernel like the device update."""
+    import torch
+    w = inputs.shallow_water_batch([16] * 20 + [8] * 9, seed=191, dx=0.05)
+    T = w.num_patches
+    b = _swe_batch(w, 1)
+    hin = torch.from_numpy(w.Q0.astype(np.float32)).pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    dx = torch.tensor(w.dx).pin_memory()
+    dt = torch.full((T,), 2e-3, dtype=torch.float64).pin_memory()
+    lam = torch.zeros(T, dtype=torch.float64).pin_memory()
+    dtn = torch.zeros_like(lam).pin_memory()
+    b.update_host(hin, hout, dx, dt, lam, dtn, 0.4, chunks)
+    qa = hin.cuda()
+    qb = qa.clone()
+    rl = torch.zeros(T, dtype=torch.float64, device="cuda")
+    rn = torch.zeros_like(rl)
+    b.update(qa, qb, dx.cuda(), dt.cuda(), rl, rn, 0.4)
+    b.status()
+    for g_, r_ in zip(patches_interior(hout.numpy(), 2, w.patch_size),
+                      patches_interior(qb.cpu().numpy(), 2, w.patch_size)):
+        assert np.array_equal(g_, r_)
+    assert np.array_equal(lam.numpy(), rl.cpu().numpy()) and np.array_equal(dtn.numpy(), rn.cpu().numpy())
+    b.close()

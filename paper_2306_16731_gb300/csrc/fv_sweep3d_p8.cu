@@ -536,8 +536,19 @@ bool fused3d_p8_applies(const BatchView &b, int precision, const void *q_in, con
     if (b.dim != 3 || b.uniform_p != kP || b.halo_mode != 1 || precision == PREC_F64) return false;
     // bulk copies need 16-byte aligned sources: buffers and patch bases
     const size_t patch_bytes = (size_t)kE * kE * kE * kN * (precision == PREC_F32 ? 4 : 2);
-    return patch_bytes % 16 == 0 && reinterpret_cast<uintptr_t>(q_in) % 16 == 0 &&
-           reinterpret_cast<uintptr_t>(q_out) % 16 == 0;
+    if (patch_bytes % 16 != 0 || reinterpret_cast<uintptr_t>(q_in) % 16 != 0 ||
+        reinterpret_cast<uintptr_t>(q_out) % 16 != 0)
+        return false;
+    // the bulk copies and stores address device memory only; mapped host
+    // buffers (the direct host-state update) take the block kernel's loads
+    for (const void *ptr : {q_in, static_cast<const void *>(q_out)}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    return true;
 }
 
 cudaError_t launch_fused3d_p8(const BatchView &b, int precision, const StepArgs &a, int first, int count,

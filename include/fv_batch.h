@@ -313,8 +313,16 @@ int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out,
  * if one met a non-physical state (and clear both). */
 int fv_batch_status(fv_batch_t *b);
 
-/* Free the batch (NULL-safe).  Synchronises its stream first. */
+/* Free the batch (NULL-safe).  Synchronises its stream first.  A handle
+ * that is not live (already destroyed, or never created) gives FV_EINVAL
+ * and is not touched. */
 int fv_batch_destroy(fv_batch_t *b);
+
+/* Test hook for the out-of-memory paths; the paper has no counterpart.
+ * k > 0 makes the k-th following device allocation of the library fail
+ * (every call then returns FV_ENOMEM and leaves its batch usable); k <= 0
+ * disarms it.  Process-wide. */
+int fv_test_fail_device_alloc(int k);
 
 /* Thread-local description of the last failure ("" if none). */
 const char *fv_last_error(void);

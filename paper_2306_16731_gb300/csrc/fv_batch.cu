@@ -14,7 +14,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -40,6 +42,9 @@ int fail(int code, const char *fmt, ...)
 
 int cuda_fail(cudaError_t e, const char *what)
 {
+    // clear the runtime's last-error state, so that a failed call does not
+    // surface again at the caller's next, unrelated CUDA call
+    cudaGetLastError();
     return fail(FV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -144,6 +149,30 @@ struct DeviceGuard {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Device allocations of the batch object go through here, so that a test
+// can make the k-th one fail (fv_test_fail_device_alloc) and check that every
+// call returns FV_ENOMEM cleanly.
+std::atomic<int> g_fail_alloc_countdown{0};
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    int k = g_fail_alloc_countdown.load();
+    while (k > 0) {
+        if (g_fail_alloc_countdown.compare_exchange_weak(k, k - 1)) {
+            if (k == 1) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+// Handles returned by fv_batch_create and not yet destroyed.
+std::mutex g_live_mu;
+std::set<const void *> g_live;
+
 bool overlaps(const void *a, const void *b, size_t bytes)
 {
     uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
@@ -155,7 +184,7 @@ int ensure_scratch(fv_batch *b)
     if (b->scratch || b->T == 0) return FV_OK;
     size_t bytes = fv::cascade_scratch_bytes(b->view, b->precision);
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = dev_alloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(FV_ENOMEM, "cascade scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
@@ -305,7 +334,7 @@ static int create_batch(fv_batch_t **out, int pde, int dim, int num_patches, con
     if (!b->items_h.empty()) memcpy(host.data() + off_items, b->items_h.data(), sizeof(fv::WorkItem) * b->items_h.size());
     if (!order.empty()) memcpy(host.data() + off_order, order.data(), 4 * order.size());
 
-    cudaError_t e = cudaMalloc(&b->meta, total);
+    cudaError_t e = dev_alloc(&b->meta, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete b;
@@ -380,6 +409,10 @@ static int create_batch(fv_batch_t **out, int pde, int dim, int num_patches, con
             return rc;
         }
     }
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        g_live.insert(b);
+    }
     *out = b;
     return FV_OK;
 }
@@ -390,6 +423,12 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches, const int32_t *p
 {
     return create_batch(out, FV_PDE_EULER, dim, num_patches, patch_size, halo, unknowns, precision, halo_mode,
                         gamma, 0.0, cuda_stream);
+}
+
+int fv_test_fail_device_alloc(int k)
+{
+    g_fail_alloc_countdown.store(k > 0 ? k : 0);
+    return FV_OK;
 }
 
 int fv_batch_create_pde(fv_batch_t **out, int pde, int dim, int num_patches, const int32_t *patch_size,
@@ -457,7 +496,7 @@ int fv_batch_set_neighbours(fv_batch_t *b, const int32_t *neighbours)
     const size_t bytes = (size_t)b->T * faces * sizeof(int32_t);
     if (!b->nbr && bytes) {
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, bytes);
+        cudaError_t e = dev_alloc(&p, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(FV_ENOMEM, "neighbour table: %s", cudaGetErrorString(e));
@@ -706,6 +745,10 @@ int fv_batch_status(fv_batch_t *b)
 int fv_batch_destroy(fv_batch_t *b)
 {
     if (!b) return FV_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        if (!g_live.erase(b)) return fail(FV_EINVAL, "not a live batch (destroyed twice?)");
+    }
     DeviceGuard dg(b->device);
     cudaStreamSynchronize(b->stream);
     drop_graphs(b);
@@ -768,20 +811,36 @@ int host_staging(fv_batch *b)
 {
     if (b->hs_in) return FV_OK;
     const size_t bytes = (size_t)b->state_elems * elem_bytes(b->precision);
-    cudaError_t e = cudaMalloc(&b->hs_in, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&b->hs_out, bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->hs_arrays, 4 * (size_t)b->T * sizeof(double));
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->hs_copy_in, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->hs_copy_out, cudaStreamNonBlocking);
+    void *in = nullptr, *out = nullptr, *arr = nullptr;
+    cudaStream_t ci = nullptr, co = nullptr;
+    std::vector<cudaEvent_t> evs;
+    cudaError_t e = dev_alloc(&in, bytes);
+    if (e == cudaSuccess) e = dev_alloc(&out, bytes);
+    if (e == cudaSuccess) e = dev_alloc(&arr, 4 * (size_t)b->T * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ci, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking);
     for (int i = 0; e == cudaSuccess && i < 2 * kMaxHostChunks + 1; ++i) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) b->hs_events.push_back(ev);
+        if (e == cudaSuccess) evs.push_back(ev);
     }
     if (e != cudaSuccess) {
+        // nothing partial stays behind: the next call starts over
         cudaGetLastError();
+        for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+        if (ci) cudaStreamDestroy(ci);
+        if (co) cudaStreamDestroy(co);
+        cudaFree(in);
+        cudaFree(out);
+        cudaFree(arr);
         return fail(FV_ENOMEM, "host-update staging: %s", cudaGetErrorString(e));
     }
+    b->hs_in = in;
+    b->hs_out = out;
+    b->hs_arrays = static_cast<double *>(arr);
+    b->hs_copy_in = ci;
+    b->hs_copy_out = co;
+    b->hs_events = evs;
     return FV_OK;
 }
 
@@ -979,7 +1038,7 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
     cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, b->device);
     const size_t flush_n = (size_t)std::max(l2_bytes, 1 << 20) * 2 / sizeof(uint4);
     uint4 *flush = nullptr;
-    if (cudaMalloc(&flush, flush_n * sizeof(uint4) + 16) != cudaSuccess) {
+    if (dev_alloc(reinterpret_cast<void **>(&flush), flush_n * sizeof(uint4) + 16) != cudaSuccess) {
         cudaGetLastError();
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -994,7 +1053,7 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
     // eigenvalue and time-step outputs as in a time-stepping loop
     double *outs = nullptr;
     std::vector<fv::FusedShape> cands;
-    if (cudaMalloc(&outs, 2 * (size_t)b->T * sizeof(double)) != cudaSuccess) {
+    if (dev_alloc(reinterpret_cast<void **>(&outs), 2 * (size_t)b->T * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         rc = fail(FV_ENOMEM, "autotune: eigenvalue/time-step scratch");
         goto done;
@@ -1107,7 +1166,7 @@ extern "C" int fv_batch_set_host_patches(fv_batch_t *b, const void *const *patch
     for (int i = 0; i < b->T; ++i)
         if (patch_in[i] == patch_out[i]) return fail(FV_EINVAL, "patch %d: input and output alias", i);
     if (!b->sp_table && b->T > 0) {
-        cudaError_t e = cudaMalloc((void **)&b->sp_table, 2 * (size_t)b->T * sizeof(void *));
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&b->sp_table), 2 * (size_t)b->T * sizeof(void *));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(FV_ENOMEM, "patch address table");

@@ -37,6 +37,7 @@ namespace fv {
 namespace {
 
 constexpr int kMaxWarpsPerBlock = 16;
+constexpr int kMaxBlockSmem = 227 * 1024;      // opt-in dynamic shared memory per block
 
 struct SweepParams {
     BatchView b;
@@ -831,10 +832,14 @@ template <typename S, int P>
 cudaError_t launch_stream(const SweepParams &sp, int wpb, cudaStream_t st)
 {
     static bool attr_set = false;
+    // warps per block limited by the shared memory a block may use (FP64
+    // rings of 16 warps would exceed it; results do not depend on the shape)
+    constexpr int kMaxWarpsSmem = kMaxBlockSmem / warp_smem_bytes2d_stream<S>();
+    wpb = std::min(wpb, kMaxWarpsSmem);
     const int bytes = wpb * warp_smem_bytes2d_stream<S>();
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep2d_stream<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxWarpsPerBlock * warp_smem_bytes2d_stream<S>());
+                                             std::min(kMaxWarpsPerBlock, kMaxWarpsSmem) * warp_smem_bytes2d_stream<S>());
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -853,10 +858,12 @@ template <typename S, int P>
 cudaError_t launch_class(const SweepParams &sp, int wpb, int bps, cudaStream_t st)
 {
     static bool attr_set = false;
+    constexpr int kMaxWarpsSmem = kMaxBlockSmem / warp_smem_bytes2d<S>();
+    wpb = std::min(wpb, kMaxWarpsSmem);
     const int bytes = wpb * warp_smem_bytes2d<S>();
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep2d<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxWarpsPerBlock * warp_smem_bytes2d<S>());
+                                             std::min(kMaxWarpsPerBlock, kMaxWarpsSmem) * warp_smem_bytes2d<S>());
         if (e != cudaSuccess) return e;
         attr_set = true;
     }

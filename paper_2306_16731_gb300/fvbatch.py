@@ -54,7 +54,7 @@ EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_ba
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
            "fv_batch_scratch_bytes", "fv_batch_describe", "fv_batch_launches_per_update",
            "fv_batch_test_wait_expiry", "fv_batch_set_cascade_layout", "fv_batch_create_pde",
-           "fv_batch_set_host_patches", "fv_patch_batch_update_scattered"]
+           "fv_batch_set_host_patches", "fv_patch_batch_update_scattered", "fv_test_fail_device_alloc"]
 
 
 class FVError(RuntimeError):
@@ -95,6 +95,7 @@ def load() -> ctypes.CDLL:
             "fv_batch_set_launch_shape": (i, [_vp, i, i]),
             "fv_batch_test_wait_expiry": (i, [_vp, i]),
             "fv_batch_set_cascade_layout": (i, [_vp, i]),
+            "fv_test_fail_device_alloc": (i, [i]),
             "fv_batch_set_host_patches": (i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
             "fv_patch_batch_update_scattered": (i, [_vp, _vp, _vp, _vp, _vp, d, i]),
             "fv_batch_set_neighbours": (i, [_vp, ctypes.POINTER(ctypes.c_int32)]),
@@ -206,6 +207,11 @@ def fv_batch_set_host_patches(b, patch_in, patch_out):
 def fv_patch_batch_update_scattered(b, dx_host, dt_host, lambda_host=None, dt_next_host=None, cfl=0.4, flags=0):
     return _check(load().fv_patch_batch_update_scattered(b, _addr(dx_host), _addr(dt_host), _addr(lambda_host),
                                                          _addr(dt_next_host), float(cfl), int(flags)))
+
+
+def fv_test_fail_device_alloc(k):
+    """Test hook: make the k-th following device allocation fail (k <= 0 disarms)."""
+    return _check(load().fv_test_fail_device_alloc(int(k)))
 
 
 def fv_batch_set_cascade_layout(b, layout):

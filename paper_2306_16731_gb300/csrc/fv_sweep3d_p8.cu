@@ -97,6 +97,15 @@ template <> struct Arith<false> {
 };
 
 __device__ __forceinline__ float2 bcast(float s) { return make_float2(s, s); }
+
+// shuffle of a packed pair as one 64-bit value (the halves land in a
+// register pair, ready for the f32x2 instructions)
+__device__ __forceinline__ float2 shfl2(float2 v, int src)
+{
+    unsigned long long u = (unsigned long long)__float_as_uint(v.x) | ((unsigned long long)__float_as_uint(v.y) << 32);
+    u = __shfl_sync(0xffffffffu, u, src);
+    return make_float2(__uint_as_float((unsigned)u), __uint_as_float((unsigned)(u >> 32)));
+}
 __device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ float2 max2(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
 
@@ -229,6 +238,9 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // every group has finished reading shared memory
 __device__ __forceinline__ void bulk_wait_read_0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 
+// all but the most recent group have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory"); }
+
 // every group has completed
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 
@@ -272,8 +284,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int W = blockDim.x >> 5;
     const unsigned bar0 = saddr(smem8) + 8u * (unsigned)(warp * kSlots);
-    // per warp: kSlots input plane slots, then the output staging buffer
-    unsigned char *slots = smem8 + ((W * kSlots * 8 + 15) & ~15) + (size_t)warp * (kSlots + 1) * G::slot;
+    // per warp: kSlots input plane slots, then two output staging buffers
+    unsigned char *slots = smem8 + ((W * kSlots * 8 + 15) & ~15) + (size_t)warp * (kSlots + 2) * G::slot;
     const unsigned slot0 = saddr(slots);
 
     const int gw = blockIdx.x * W + warp, nwarps = gridDim.x * W;
@@ -309,6 +321,35 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
     const int src_r = (lane & 24) | ((x + 1) & 7), src_l = (lane & 24) | ((x + 7) & 7);
     const int src_u = (lane + 8) & 31, src_d = (lane + 24) & 31;
     const float2 g2 = bcast(sp.gamma), gm12 = bcast(sp.gm1);
+    // the wrapped x-halo column this lane's volumes are copied to as well
+    // (column 8 -> column 0, column 1 -> column 9), or none
+    const int halo_col = x == kP - 1 ? 0 : (x == 0 ? kP + 1 : -1);
+
+    // Output staging: the plane finished in step t is assembled in buffer
+    // t & 1 and leaves at the start of step t + 1 (after the one warp
+    // barrier of that step), so assembling never waits for a store.
+    unsigned char *const stg0 = slots + kSlots * G::slot;
+    // Publish the plane assembled in the previous step: called by every lane
+    // after the step's barrier; lane 0 has issued the bulk store of the
+    // 16-byte aligned middle, the lanes write the ragged ends.
+    auto store_ends = [&](int64_t opatch, int zf, int buf) {
+        const unsigned char *stg = stg0 + buf * G::slot;
+        const int sa = G::rows_begin(zf) & 15;
+        unsigned char *gbase = sp.q_out + opatch * G::patch + (G::rows_begin(zf) - sa);   // 16-aligned
+        constexpr int kRows = 8 * G::row;
+        const int mlo = (sa + 15) & ~15, end = sa + kRows, mhi = end & ~15;
+        const int o = lane < 16 ? sa + 2 * lane : mhi + 2 * (lane - 16);
+        if (lane < 16 ? o < mlo : o < end)
+            *reinterpret_cast<unsigned short *>(gbase + o) = *reinterpret_cast<const unsigned short *>(stg + o);
+    };
+    auto store_middle = [&](int64_t opatch, int zf, int buf) {     // lane 0
+        const int sa = G::rows_begin(zf) & 15;
+        unsigned char *gbase = sp.q_out + opatch * G::patch + (G::rows_begin(zf) - sa);
+        constexpr int kRows = 8 * G::row;
+        const int mlo = (sa + 15) & ~15, mhi = (sa + kRows) & ~15;
+        bulk_s2g(gbase + mlo, saddr(stg0 + buf * G::slot) + (unsigned)mlo, (unsigned)(mhi - mlo));
+        bulk_commit();
+    };
 
     // carried from the previous plane: state, F_z, lambda_z, its x/y face
     // difference and its lower z face
@@ -327,12 +368,24 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
         float2 lmax = bcast(0.0f);
 #pragma unroll
         for (int s = 0; s < kStepsPerPatch; ++s) {
-            __syncwarp();                               // slot of step s-1 consumed by all lanes
-            {
+            // the previous step's output plane, if it made one: plane s - 3 of
+            // this patch, or plane 7 of the warp's previous patch
+            const bool prev_out = s >= 3 || (s == 0 && pi > 0);
+            const int64_t opatch = s == 0 ? patch - nwarps : patch;
+            const int ozf = s == 0 ? kP - 1 : s - 3;
+            const int obuf = (s + 1) & 1;
+            if (prev_out) fence_proxy_async_smem();     // this lane's staging writes -> async proxy
+            __syncwarp();                               // slot of step s-1 consumed, staging complete
+            if (lane == 0) {
                 const int sn = s + kSlots - 1;
                 if (sn < kStepsPerPatch) issue(patch, (sn + kP - 1) & (kP - 1), sn % kSlots, 0u);
                 else if (has_next) issue(patch + nwarps, (sn - kStepsPerPatch + kP - 1) & (kP - 1), sn % kSlots, 0u);
+                if (prev_out) store_middle(opatch, ozf, obuf);
+                bulk_wait_read_1();                     // the store before it has read its buffer
             }
+            if (prev_out) store_ends(opatch, ozf, obuf);
+            // the vote also orders every lane's staging writes below after
+            // lane 0's wait above
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar0 + 8u * (s % kSlots), (s / kSlots) & 1))) {
                 waited = pi * kStepsPerPatch + s;
                 goto timeout;
@@ -366,46 +419,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
 #pragma unroll
                 for (int k = 0; k < kN; ++k) qn[k] = A::fma(nsc, A::add(d[k], sub2<Pk>(Fzl[k], Flo[k])), qp[k]);
                 // rows 0..7 of the plane (x-halo volumes included) are one
-                // contiguous byte range; it is assembled in a staging buffer
-                // laid out like an input slot (range start at offset sa =
-                // start mod 16) and written by one bulk store of its 16-byte
-                // aligned middle plus 2-byte stores of the ragged ends
-                unsigned char *stg = slots + kSlots * G::slot;
-                if (lane == 0) bulk_wait_read_0();      // the previous plane's store has read the buffer
-                __syncwarp();
-                const int sa = G::rows_begin(zf) & 15;
-                S *ra = reinterpret_cast<S *>(stg + sa + (2 * j) * G::row);
-                S *rb = reinterpret_cast<S *>(stg + sa + (2 * j + 1) * G::row);
+                // contiguous byte range, assembled in staging buffer s & 1
+                // laid out like an input slot (range start at offset
+                // start mod 16); the lanes of columns 8 and 1 also fill the
+                // wrapped x-halo columns 0 and 9
+                unsigned char *stg = stg0 + (s & 1) * G::slot + (G::rows_begin(zf) & 15);
+                S *ra = reinterpret_cast<S *>(stg + (2 * j) * G::row);
+                S *rb = reinterpret_cast<S *>(stg + (2 * j + 1) * G::row);
                 store_pair<S>(ra + (x + 1) * kN, rb + (x + 1) * kN, qn);
-                __syncwarp();
-                // x-halo volumes: lane r < 8 copies column 8 of row r to the
-                // -x halo (column 0), lane 8 + r column 1 to the +x halo
-                // (column 9); the 16 source words of each unknown fall in
-                // distinct banks
-                if (lane < 16) {
-                    const int r = lane & 7, up = lane >> 3;
-                    S *row = reinterpret_cast<S *>(stg + sa + r * G::row);
-                    const S *src = row + (up ? 1 : kP) * kN;
-                    S *dst = row + (up ? kP + 1 : 0) * kN;
-                    S v[kN];
-#pragma unroll
-                    for (int k = 0; k < kN; ++k) v[k] = src[k];
-#pragma unroll
-                    for (int k = 0; k < kN; ++k) dst[k] = v[k];
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                unsigned char *gbase = sp.q_out + patch * G::patch + (G::rows_begin(zf) - sa);   // 16-aligned
-                constexpr int kRows = 8 * G::row;
-                const int mlo = (sa + 15) & ~15, end = sa + kRows, mhi = end & ~15;
-                if (lane == 0) {
-                    bulk_s2g(gbase + mlo, saddr(stg) + (unsigned)mlo, (unsigned)(mhi - mlo));
-                    bulk_commit();
-                }
-                const int o = lane < 16 ? sa + 2 * lane : mhi + 2 * (lane - 16);
-                if (lane < 16 ? o < mlo : o < end)
-                    *reinterpret_cast<unsigned short *>(gbase + o) =
-                        *reinterpret_cast<const unsigned short *>(stg + o);
+                if (halo_col >= 0) store_pair<S>(ra + halo_col * kN, rb + halo_col * kN, qn);
                 const Prim2 sn = prim2<Pk>(qn, g2, gm12);
                 const float2 l = A::add(max2(max2(abs2(sn.u[0]), abs2(sn.u[1])), abs2(sn.u[2])), sn.c);
                 lmax = max2(lmax, l);
@@ -431,23 +453,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
                 flux2<0, Pk>(q, st, Fx);
                 const float2 lx = lam2<Pk>(st.u[0], st.c);
 #pragma unroll
-                for (int k = 0; k < kN; ++k)
-                    nq[k] = make_float2(__shfl_sync(0xffffffffu, q[k].x, src_r),
-                                        __shfl_sync(0xffffffffu, q[k].y, src_r));
+                for (int k = 0; k < kN; ++k) nq[k] = shfl2(q[k], src_r);
                 nF[0] = nq[1];
 #pragma unroll
-                for (int k = 1; k < kN; ++k)
-                    nF[k] = make_float2(__shfl_sync(0xffffffffu, Fx[k].x, src_r),
-                                        __shfl_sync(0xffffffffu, Fx[k].y, src_r));
-                const float2 nl = make_float2(__shfl_sync(0xffffffffu, lx.x, src_r),
-                                              __shfl_sync(0xffffffffu, lx.y, src_r));
+                for (int k = 1; k < kN; ++k) nF[k] = shfl2(Fx[k], src_r);
+                const float2 nl = shfl2(lx, src_r);
                 face2<Pk>(q, nq, Fx, nF, lx, nl, Fr);
 #pragma unroll
-                for (int k = 0; k < kN; ++k) {
-                    const float2 Fl = make_float2(__shfl_sync(0xffffffffu, Fr[k].x, src_l),
-                                                  __shfl_sync(0xffffffffu, Fr[k].y, src_l));
-                    d[k] = sub2<Pk>(Fr[k], Fl);
-                }
+                for (int k = 0; k < kN; ++k) d[k] = sub2<Pk>(Fr[k], shfl2(Fr[k], src_l));
             }
             // y faces: (row 2j | 2j+1) in the lane, (row 2j+1 | 2j+2) with
             // lane + 8; the face below row 2j is the face above row 2j-1 of
@@ -471,6 +484,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, FV_P8_MIN_BLOCKS) k_sweep3d_p8
             }
         }
     }
+    // the last plane of the warp's last patch
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) store_middle(patch0 + (int64_t)(mine - 1) * nwarps, kP - 1, 1);
+    store_ends(patch0 + (int64_t)(mine - 1) * nwarps, kP - 1, 1);
     if (lane == 0) bulk_wait_all();                    // output stores complete, staging free
     {
         const bool bad = !(min_rp > 0.0f) || !(sum_l.x + sum_l.y < INFINITY);
@@ -499,7 +517,7 @@ size_t slot_bytes_for(int precision)
 size_t smem_bytes_for(int warps, int precision)
 {
     return (((size_t)warps * kSlots * 8 + 15) & ~size_t(15)) +
-           (size_t)warps * (kSlots + 1) * slot_bytes_for(precision);
+           (size_t)warps * (kSlots + 2) * slot_bytes_for(precision);
 }
 
 template <typename S>

@@ -591,15 +591,21 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
             shfl_vec<N>(nF, FxB, 1, true);
             nl = __shfl_down_sync(0xffffffffu, lxB, 1);
             rusanov2<N>(qB, nq, FxB, nF, lxB, nl, FrB);
+            // every lane reads one edge entry per row (side 1 for column 7,
+            // side 0 otherwise), so the edge columns cost one set of loads
+            C eA[N], eB[N];
+            const int ex = (x == 7 ? 8 : 0) + yb;
+#pragma unroll
+            for (int k = 0; k < N; ++k) { eA[k] = bf[ex * N + k]; eB[k] = bf[(ex + 4) * N + k]; }
             if (x == 7) {
 #pragma unroll
-                for (int k = 0; k < N; ++k) { FrA[k] = bf[(8 + yb) * N + k]; FrB[k] = bf[(12 + yb) * N + k]; }
+                for (int k = 0; k < N; ++k) { FrA[k] = eA[k]; FrB[k] = eB[k]; }
             }
             shfl_vec<N>(FlA, FrA, 1, false);
             shfl_vec<N>(FlB, FrB, 1, false);
             if (x == 0) {
 #pragma unroll
-                for (int k = 0; k < N; ++k) { FlA[k] = bf[yb * N + k]; FlB[k] = bf[(4 + yb) * N + k]; }
+                for (int k = 0; k < N; ++k) { FlA[k] = eA[k]; FlB[k] = eB[k]; }
             }
 #pragma unroll
             for (int k = 0; k < N; ++k) { dA[k] = FrA[k] - FlA[k]; dB[k] = FrB[k] - FlB[k]; }
@@ -633,9 +639,12 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
             shfl_vec<N>(nF, FyB, 8, true);
             nl = __shfl_down_sync(0xffffffffu, lyB, 8);
             rusanov2<N>(qB, nq, FyB, nF, lyB, nl, FuB);
+            C ey[N];                                          // side 3 for the top row, side 2 otherwise
+#pragma unroll
+            for (int k = 0; k < N; ++k) ey[k] = bf[((top ? 24 : 16) + x) * N + k];
             if (top) {
 #pragma unroll
-                for (int k = 0; k < N; ++k) FuB[k] = bf[(24 + x) * N + k];
+                for (int k = 0; k < N; ++k) FuB[k] = ey[k];
             }
             // lower faces: the lower lane's upper faces; row 4 (B of the bottom
             // lane row) takes the upper face of row 3 (A of lane + 24)
@@ -644,7 +653,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
             shfl_vec<N>(t, FuA, 24, true);
             if (bottom) {
 #pragma unroll
-                for (int k = 0; k < N; ++k) { FdA[k] = bf[(16 + x) * N + k]; FdB[k] = t[k]; }
+                for (int k = 0; k < N; ++k) { FdA[k] = ey[k]; FdB[k] = t[k]; }
             }
 #pragma unroll
             for (int k = 0; k < N; ++k) { dA[k] += FuA[k] - FdA[k]; dB[k] += FuB[k] - FdB[k]; }

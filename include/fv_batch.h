@@ -257,7 +257,12 @@ int fv_patch_batch_update(fv_batch_t *b, const void *Q_in, void *Q_out,
  * the updates; any other batch runs as one chunk.  The first such call
  * creates the device staging (two state buffers and four arrays of
  * num_patches doubles) and two copy streams, kept until fv_batch_destroy
- * (FV_ENOMEM).
+ * (FV_ENOMEM).  When all host buffers are page-locked, the copies and
+ * updates of a call are captured once as a CUDA graph, cached per set of
+ * host buffers (and chunks, cfl, form) and replayed by later calls with the
+ * same buffers; a cached graph is dropped when a buffer is no longer
+ * page-locked, and by the calls that drop the update graphs (form, launch
+ * shape, tuning, neighbour table).
  * Synchronous: returns when Q_out_host and the outputs are complete.  The
  * halo volumes of Q_out_host are unspecified.
  */

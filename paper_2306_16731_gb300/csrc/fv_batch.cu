@@ -819,7 +819,7 @@ int host_staging(fv_batch *b)
     if (e == cudaSuccess) e = dev_alloc(&arr, 4 * (size_t)b->T * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ci, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking);
-    for (int i = 0; e == cudaSuccess && i < 2 * kMaxHostChunks + 1; ++i) {
+    for (int i = 0; e == cudaSuccess && i < 2 * kMaxHostChunks + 2; ++i) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) evs.push_back(ev);
@@ -842,6 +842,89 @@ int host_staging(fv_batch *b)
     b->hs_copy_out = co;
     b->hs_events = evs;
     return FV_OK;
+}
+
+struct HostPipeline {
+    const void *q_in;
+    void *q_out;
+    const double *dx, *dt;
+    double *lambda, *dt_next;
+    double cfl;
+    int chunks;
+    bool split;
+};
+
+bool page_locked(const void *p)
+{
+    if (!p) return true;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+bool all_page_locked(const HostPipeline &hp)
+{
+    return page_locked(hp.q_in) && page_locked(hp.q_out) && page_locked(hp.dx) && page_locked(hp.dt) &&
+           page_locked(hp.lambda) && page_locked(hp.dt_next);
+}
+
+// Enqueue one host-state update on stream `org`: dx and dt of every patch in
+// once, then per chunk its state in (copy-in stream), its update (org) and
+// its state out (copy-out stream), so the copies of neighbouring chunks
+// overlap the updates and each other; the per-patch outputs leave once
+// after the last update; the copy streams join `org` at the end.
+int enqueue_host_pipeline(fv_batch *b, cudaStream_t org, const HostPipeline &hp)
+{
+    const size_t es = elem_bytes(b->precision);
+    double *d_dx = b->hs_arrays, *d_dt = d_dx + b->T, *d_lam = d_dt + b->T, *d_dtn = d_lam + b->T;
+    unsigned char *qi = static_cast<unsigned char *>(b->hs_in), *qo = static_cast<unsigned char *>(b->hs_out);
+    const unsigned char *hi = static_cast<const unsigned char *>(hp.q_in);
+    unsigned char *ho = static_cast<unsigned char *>(hp.q_out);
+    const int C = hp.chunks;
+    const int per_item = hp.split ? (b->plan.kernel == fv::FUSED_SWEEP2D ? 32 / b->view.uniform_p : 1) : b->T;
+    const size_t arr = (size_t)b->T * sizeof(double);
+    cudaEvent_t start = b->hs_events[2 * kMaxHostChunks], joined = b->hs_events[2 * kMaxHostChunks + 1];
+    cudaError_t e = cudaEventRecord(start, org);      // order after earlier work on the stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hs_copy_in, start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hs_copy_out, start, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_dx, hp.dx, arr, cudaMemcpyHostToDevice, b->hs_copy_in);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_dt, hp.dt, arr, cudaMemcpyHostToDevice, b->hs_copy_in);
+    for (int c = 0; c < C && e == cudaSuccess; ++c) {
+        const int item_lo = hp.split ? (int)((int64_t)b->plan.num_items * c / C) : 0;
+        const int item_hi = hp.split ? (int)((int64_t)b->plan.num_items * (c + 1) / C) : 0;
+        const int p_lo = hp.split ? std::min(b->T, item_lo * per_item) : 0;
+        const int p_hi = hp.split ? std::min(b->T, item_hi * per_item) : b->T;
+        const size_t o = (size_t)b->elem_off[p_lo] * es, n = (size_t)(b->elem_off[p_hi] - b->elem_off[p_lo]) * es;
+        cudaEvent_t ev_in = b->hs_events[2 * c], ev_done = b->hs_events[2 * c + 1];
+        e = cudaMemcpyAsync(qi + o, hi + o, n, cudaMemcpyHostToDevice, b->hs_copy_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in, b->hs_copy_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(org, ev_in, 0);
+        if (e != cudaSuccess) break;
+        fv::StepArgs args{qi, qo, d_dx, d_dt, hp.lambda ? d_lam : nullptr, hp.dt_next ? d_dtn : nullptr, hp.cfl};
+        if (hp.split) {
+            fv::FusedPlan sub = b->plan;
+            sub.num_classes = 1;
+            sub.class_begin[0] = item_lo;
+            sub.class_end[0] = item_hi;
+            e = fv::launch_fused_update(b->view, b->precision, args, sub, org);
+            if (e != cudaSuccess) return cuda_fail(e, "host update launch");
+        } else {
+            const int rc = launch_update(b, org, qi, qo, d_dx, d_dt, args.lambda_out, args.dt_next_out, hp.cfl);
+            if (rc) return rc;
+        }
+        e = cudaEventRecord(ev_done, org);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hs_copy_out, ev_done, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ho + o, qo + o, n, cudaMemcpyDeviceToHost, b->hs_copy_out);
+    }
+    if (e == cudaSuccess && hp.lambda) e = cudaMemcpyAsync(hp.lambda, d_lam, arr, cudaMemcpyDeviceToHost, b->hs_copy_out);
+    if (e == cudaSuccess && hp.dt_next)
+        e = cudaMemcpyAsync(hp.dt_next, d_dtn, arr, cudaMemcpyDeviceToHost, b->hs_copy_out);
+    if (e == cudaSuccess) e = cudaEventRecord(joined, b->hs_copy_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(org, joined, 0);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "host update enqueue");
 }
 
 }  // namespace
@@ -882,62 +965,51 @@ extern "C" int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, 
     }
     int rc = host_staging(b);
     if (rc) return rc;
-    const size_t es = elem_bytes(b->precision);
-    double *d_dx = b->hs_arrays, *d_dt = d_dx + b->T, *d_lam = d_dt + b->T, *d_dtn = d_lam + b->T;
-    unsigned char *qi = static_cast<unsigned char *>(b->hs_in), *qo = static_cast<unsigned char *>(b->hs_out);
-    const unsigned char *hi = static_cast<const unsigned char *>(Q_in_host);
-    unsigned char *ho = static_cast<unsigned char *>(Q_out_host);
-
     // Chunks are ranges of work items of a uniform fused batch (so each
     // chunk's update is one launch over its own patches); any other batch
     // runs as a single chunk.
     const bool split = b->form == FV_FORM_FUSED && b->view.uniform_p > 0 && b->plan.num_classes == 1 &&
                        !b->view.nbr && chunks > 1;
     const int C = split ? std::min(chunks, b->plan.num_items) : 1;
-    const int per_item = split ? (b->plan.kernel == fv::FUSED_SWEEP2D ? 32 / b->view.uniform_p : 1) : b->T;
-    cudaEvent_t start = b->hs_events[2 * kMaxHostChunks];
-    cudaError_t e = cudaEventRecord(start, b->stream);      // order after earlier work on the batch stream
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hs_copy_in, start, 0);
-    for (int c = 0; c < C && e == cudaSuccess; ++c) {
-        const int item_lo = split ? (int)((int64_t)b->plan.num_items * c / C) : 0;
-        const int item_hi = split ? (int)((int64_t)b->plan.num_items * (c + 1) / C) : 0;
-        const int p_lo = split ? std::min(b->T, item_lo * per_item) : 0;
-        const int p_hi = split ? std::min(b->T, item_hi * per_item) : b->T;
-        const size_t o = (size_t)b->elem_off[p_lo] * es, n = (size_t)(b->elem_off[p_hi] - b->elem_off[p_lo]) * es;
-        const size_t a = (size_t)p_lo * sizeof(double), an = (size_t)(p_hi - p_lo) * sizeof(double);
-        cudaEvent_t ev_in = b->hs_events[2 * c], ev_done = b->hs_events[2 * c + 1];
-        e = cudaMemcpyAsync(qi + o, hi + o, n, cudaMemcpyHostToDevice, b->hs_copy_in);
-        if (e == cudaSuccess) e = cudaMemcpyAsync((unsigned char *)d_dx + a, (const unsigned char *)dx_host + a, an,
-                                                  cudaMemcpyHostToDevice, b->hs_copy_in);
-        if (e == cudaSuccess) e = cudaMemcpyAsync((unsigned char *)d_dt + a, (const unsigned char *)dt_host + a, an,
-                                                  cudaMemcpyHostToDevice, b->hs_copy_in);
-        if (e == cudaSuccess) e = cudaEventRecord(ev_in, b->hs_copy_in);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev_in, 0);
-        if (e != cudaSuccess) break;
-        fv::StepArgs args{qi, qo, d_dx, d_dt, lambda_host ? d_lam : nullptr, dt_next_host ? d_dtn : nullptr, cfl};
-        if (split) {
-            fv::FusedPlan sub = b->plan;
-            sub.num_classes = 1;
-            sub.class_begin[0] = item_lo;
-            sub.class_end[0] = item_hi;
-            e = fv::launch_fused_update(b->view, b->precision, args, sub, b->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "host update launch");
-        } else {
-            rc = launch_update(b, b->stream, qi, qo, d_dx, d_dt, args.lambda_out, args.dt_next_out, cfl);
-            if (rc) return rc;
-        }
-        e = cudaEventRecord(ev_done, b->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hs_copy_out, ev_done, 0);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(ho + o, qo + o, n, cudaMemcpyDeviceToHost, b->hs_copy_out);
-        if (e == cudaSuccess && lambda_host)
-            e = cudaMemcpyAsync((unsigned char *)lambda_host + a, (const unsigned char *)d_lam + a, an,
-                                cudaMemcpyDeviceToHost, b->hs_copy_out);
-        if (e == cudaSuccess && dt_next_host)
-            e = cudaMemcpyAsync((unsigned char *)dt_next_host + a, (const unsigned char *)d_dtn + a, an,
-                                cudaMemcpyDeviceToHost, b->hs_copy_out);
+    HostPipeline hp{Q_in_host, Q_out_host, dx_host, dt_host, lambda_host, dt_next_host, cfl, C, split};
+
+    // The pipeline is captured once per set of host buffers as a CUDA graph
+    // (one launch per call instead of several runtime calls per chunk); the
+    // buffers must still be page-locked when a cached graph is replayed.
+    const GraphKey key{Q_in_host, Q_out_host, dx_host, dt_host, dt_next_host, lambda_host, -1000 - C, cfl, b->form};
+    auto it = b->graphs.find(key);
+    if (it != b->graphs.end() && !all_page_locked(hp)) {
+        cudaGraphExecDestroy(it->second);
+        b->graphs.erase(it);
+        it = b->graphs.end();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->hs_copy_out);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaGraphExec_t exec = it != b->graphs.end() ? it->second : nullptr;
+    if (!exec && all_page_locked(hp)) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = enqueue_host_pipeline(b, b->capture_stream, hp);
+            e = cudaStreamEndCapture(b->capture_stream, &graph);
+            if (rc == FV_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (rc != FV_OK || e != cudaSuccess) exec = nullptr;
+        }
+        if (exec) {
+            b->graphs[key] = exec;
+        } else {
+            // not capturable (e.g. the task-graph form): run it eagerly
+            cudaGetLastError();
+            g_last_error.clear();
+        }
+    }
+    if (exec) {
+        cudaError_t e = cudaGraphLaunch(exec, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        return e == cudaSuccess ? FV_OK : cuda_fail(e, "host update");
+    }
+    rc = enqueue_host_pipeline(b, b->stream, hp);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? FV_OK : cuda_fail(e, "host update");
 }
 

@@ -1063,3 +1063,52 @@ def test_non_finite_time_step_is_reported():
             b.status()
         assert e.value.code == fb.FV_ENONPHYSICAL
         b.close()
+
+
+def test_host_update_graph_replays_new_contents_and_falls_back_for_pageable_buffers():
+    """The chunked host-state update is captured as a CUDA graph per set of
+    host buffers and replayed: a replay must read the buffers' current
+    contents (a chain of steps through the same two buffers, fixed halos put
+    back between steps, equals the same chain of device updates), a change
+    of launch shape drops the graph, and pageable buffers (not capturable)
+    run the same pipeline eagerly."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(2, [16] * 600, seed=141, dx=0.02)
+    T = w.num_patches
+    b = fb.FVBatch(2, w.patch_size, precision=fb.FV_F32)
+    dx = torch.tensor(w.dx, device="cuda")
+    dt = torch.full((T,), 1e-3, dtype=torch.float64, device="cuda")
+    # device reference: three steps, ping-pong
+    qs = [torch.from_numpy(w.Q0).to("cuda", torch.float32), None]
+    qs[1] = qs[0].clone()
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    for s in range(3):
+        b.update(qs[s & 1], qs[1 - (s & 1)], dx, dt, lam, None, 0.4)
+    torch.cuda.synchronize()
+    ref = patches_interior(qs[1].to(torch.float64).cpu().numpy(), 2, w.patch_size)
+    ref_lam = lam.cpu().numpy().copy()
+
+    def host_chain(pin, shape_change=False):
+        mk = (lambda t: t.pin_memory()) if pin else (lambda t: t)
+        h = [mk(torch.from_numpy(w.Q0.astype(np.float32))), None]
+        h[1] = mk(h[0].clone())
+        hdx, hdt = mk(dx.cpu()), mk(dt.cpu())
+        hl = mk(torch.zeros(T, dtype=torch.float64))
+        q0 = w.Q0.astype(np.float32).reshape(T, 18, 18, 4)
+        for s in range(3):
+            if shape_change and s == 1:
+                b.set_launch_shape(2, 0)
+            b.update_host(h[s & 1], h[1 - (s & 1)], hdx, hdt, hl, None, 0.4, 4)
+            # the halos of Q_out_host are unspecified: put the fixed halos
+            # back before the buffer is the next step's input
+            o = h[1 - (s & 1)].numpy().reshape(T, 18, 18, 4)
+            o[:, [0, 17]] = q0[:, [0, 17]]
+            o[:, :, [0, 17]] = q0[:, :, [0, 17]]
+        return patches_interior(h[1].to(torch.float64).numpy(), 2, w.patch_size), hl.numpy()
+
+    for pin, change in ((True, False), (True, True), (False, False)):
+        got, gl = host_chain(pin, change)
+        assert all(np.array_equal(g, r) for g, r in zip(got, ref)), (pin, change)
+        assert np.array_equal(gl, ref_lam), (pin, change)
+    b.close()

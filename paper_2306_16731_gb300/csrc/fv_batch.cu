@@ -140,6 +140,7 @@ struct DeviceGuard {
     {
         if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
         if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+        if (!ok) cudaGetLastError();      // reported by the caller as FV_ECUDA
     }
     ~DeviceGuard()
     {
@@ -453,6 +454,7 @@ int fv_batch_set_form(fv_batch_t *b, int form)
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     if (b->view.pde != fv::PDE_EULER && form != FV_FORM_TILE)
         return fail(FV_EUNSUPPORTED, "this PDE runs on the generic patch-wise kernel (FV_FORM_TILE) only");
     if (form == FV_FORM_CASCADE || form == FV_FORM_TASKGRAPH) {
@@ -476,6 +478,7 @@ int fv_batch_set_neighbours(fv_batch_t *b, const int32_t *neighbours)
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     if (!neighbours) {
         if (b->nbr) cudaFree(b->nbr);
         b->nbr = nullptr;
@@ -519,6 +522,7 @@ int fv_halo_exchange(fv_batch_t *b, void *Q)
     if (!b->view.nbr) return fail(FV_EINVAL, "no neighbour table registered (fv_batch_set_neighbours)");
     if (!Q) return fail(FV_EINVAL, "state pointer is NULL");
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     cudaError_t e = fv::launch_halo_exchange(b->view, b->precision, b->view.nbr, Q, b->stream);
     return e == cudaSuccess ? FV_OK : cuda_fail(e, "halo exchange launch");
 }
@@ -628,6 +632,7 @@ int fv_patch_batch_update(fv_batch_t *b, const void *Q_in, void *Q_out, const do
     int rc = check_update_args(b, Q_in, Q_out, dx, dt, dt_next_out, cfl);
     if (rc) return rc;
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     return launch_update(b, b->stream, Q_in, Q_out, dx, dt, lambda_out, dt_next_out, cfl);
 }
 
@@ -638,6 +643,7 @@ int fv_max_eigenvalue(fv_batch_t *b, const void *Q, double *lambda_out)
     if (!Q || !lambda_out) return fail(FV_EINVAL, "NULL pointer");
     if (!aligned16(Q)) return fail(FV_EINVAL, "state buffer must be 16-byte aligned");
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     cudaError_t e = b->view.pde == fv::PDE_EULER
                         ? fv::launch_max_eigenvalue(b->view, b->precision, Q, lambda_out, b->stream)
                         : fv::launch_pde_max_eigenvalue(b->view, b->precision, Q, lambda_out, b->stream);
@@ -651,6 +657,7 @@ int fv_cfl_time_step(fv_batch_t *b, const double *lambda, const double *dx, doub
     if (!lambda || !dx || !dt_out) return fail(FV_EINVAL, "NULL pointer");
     if (!(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     cudaError_t e = fv::launch_cfl_time_step(b->view, lambda, dx, cfl, dt_out, b->stream);
     return e == cudaSuccess ? FV_OK : cuda_fail(e, "cfl launch");
 }
@@ -661,6 +668,7 @@ int fv_conserved_totals(fv_batch_t *b, const void *Q, double *totals_out)
     if (b->T == 0) return FV_OK;
     if (!Q || !totals_out) return fail(FV_EINVAL, "NULL pointer");
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     cudaError_t e = fv::launch_conserved_totals(b->view, b->precision, Q, totals_out, b->stream);
     return e == cudaSuccess ? FV_OK : cuda_fail(e, "totals launch");
 }
@@ -693,6 +701,7 @@ int fv_batch_run(fv_batch_t *b, void *Q_a, void *Q_b, const double *dx, double *
     if (b->T > 0 && !dt_b) return fail(FV_EINVAL, "dt_b is NULL");
     if (steps == 0 || b->T == 0) return FV_OK;
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     // the task-graph form launches one graph per step already
     if (!use_graph || b->form == FV_FORM_TASKGRAPH)
         return enqueue_steps(b, b->stream, Q_a, Q_b, dx, dt_a, dt_b, lambda_out, steps, cfl);
@@ -726,6 +735,7 @@ int fv_batch_status(fv_batch_t *b)
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     unsigned flags = 0;
@@ -939,6 +949,7 @@ extern "C" int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, 
     if (dt_next_host && !(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
     if (chunks < 0 || chunks > kMaxHostChunks) return fail(FV_EINVAL, "chunks must be in [0, %d]", kMaxHostChunks);
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     if (chunks == 0) {
         // direct: the kernels read and write the page-locked host buffers
         // through their device mappings (coherent host memory), no staging
@@ -1082,6 +1093,7 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
     if (rc) return rc;
     if (b->T == 0 || b->fused_kernel == fv::FUSED_NONE) return FV_OK;
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     std::string key = tune_key(b);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1215,6 +1227,7 @@ extern "C" int fv_batch_set_host_patches(fv_batch_t *b, const void *const *patch
 {
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     if (!patch_in && !patch_out) {
         b->sp_in.clear();
         b->sp_out.clear();
@@ -1267,6 +1280,7 @@ extern "C" int fv_patch_batch_update_scattered(fv_batch_t *b, const double *dx_h
     if (dt_next_host && !(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
     if (flags & ~(FV_SCATTER_SWAP | FV_SCATTER_COPIES)) return fail(FV_EINVAL, "unknown flags 0x%x", flags);
     DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
     int rc = host_staging(b);
     if (rc) return rc;
     const bool swap = flags & FV_SCATTER_SWAP, copies = flags & FV_SCATTER_COPIES;

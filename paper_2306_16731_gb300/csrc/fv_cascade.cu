@@ -16,6 +16,17 @@ namespace fv {
 
 namespace {
 
+// dt / (2h) in the compute type: in FP32 from the rounded operands (every
+// thread forms it, and an FP64 division per warp queues on GB300's slow
+// FP64 unit); in FP64 exactly.
+template <typename C> __device__ __forceinline__ C cascade_half_ratio(double dt, double h);
+template <> __device__ __forceinline__ float cascade_half_ratio<float>(double dt, double h)
+{
+    return __fdividef(float(dt), 2.0f * float(h));
+}
+template <> __device__ __forceinline__ double cascade_half_ratio<double>(double dt, double h) { return dt / (2.0 * h); }
+
+
 constexpr int kThreads = 256;
 
 // Layout of the per-face and per-volume vector temporaries (F_n and the face
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_update(BatchView b, const S *__res
                 acc[k] += face[Layout<L>::at(n, cell + stride, k, pad, N)] - face[Layout<L>::at(n, cell, k, pad, N)];
         }
         const double h = __ldg(dx + c.patch), tau = __ldg(dt + c.patch);
-        const C s = C(tau / (2.0 * h));
+        const C s = cascade_half_ratio<C>(tau, h);
         C qv[N];
         const int64_t eo = __ldg(b.elem_off + c.patch) + c.local * N;
         load_volume<N>(q + eo, qv);

@@ -80,6 +80,16 @@ __device__ __forceinline__ void face2(const P &ph, const C (&qL)[P::N], const C 
     for (int k = 0; k < P::N; ++k) Fh[k] = k < P::NV ? (FL[k] + FR[k]) - lam * (qR[k] - qL[k]) : C(0);
 }
 
+// dt / h in the compute type: in FP32 from the rounded operands (every
+// thread forms it, and GB300's FP64 unit would queue 8 warps' FP64
+// divisions per patch); in FP64 exactly.
+template <typename C> __device__ __forceinline__ C step_ratio(double tau, double h);
+template <> __device__ __forceinline__ float step_ratio<float>(double tau, double h)
+{
+    return __fdividef(float(tau), float(h));
+}
+template <> __device__ __forceinline__ double step_ratio<double>(double tau, double h) { return tau / h; }
+
 template <class P, typename S, typename C>
 __global__ void __launch_bounds__(kThreads) k_tile_pde(BatchView b, P ph, const S *__restrict__ q,
                                                        S *__restrict__ qout, const double *__restrict__ dx,
@@ -105,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_pde(BatchView b, P ph, const 
         __syncthreads();
 
         const double h = __ldg(dx + i), tau = __ldg(dt + i);
-        const C scale = C(tau / h), ct = C(tau);
+        const C scale = step_ratio<C>(tau, h), ct = C(tau);
         S *dst = qout + __ldg(b.elem_off + i);
         C lmax = C(0);
         bool bad = false;

@@ -11,6 +11,17 @@ namespace fv {
 
 namespace {
 
+// dt / (2h) in the compute type: in FP32 from the rounded operands (every
+// thread forms it, and an FP64 division per warp queues on GB300's slow
+// FP64 unit); in FP64 exactly.
+template <typename C> __device__ __forceinline__ C tile_half_ratio(double dt, double h);
+template <> __device__ __forceinline__ float tile_half_ratio<float>(double dt, double h)
+{
+    return __fdividef(float(dt), 2.0f * float(h));
+}
+template <> __device__ __forceinline__ double tile_half_ratio<double>(double dt, double h) { return dt / (2.0 * h); }
+
+
 constexpr int kThreads = 256;
 constexpr int kMaxPerThread = 8;              // interior volumes per thread
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -40,6 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(BatchView b, const S *__restr
     C *Fs = Qs + (size_t)cells_max * N;         // [cells][N] F_n of the current direction
     C *Ls = Fs + (size_t)cells_max * N;         // [cells]    lambda_n of the current direction
     __shared__ C red[32];
+    __shared__ C s_sc;                               // dt / (2h) of the patch
     const Gas<C> g{C(b.gamma), C(b.gamma - 1.0)};
     const bool periodic = b.halo_mode == 1;
 
@@ -66,6 +78,8 @@ __global__ void __launch_bounds__(kThreads) k_tile(BatchView b, const S *__restr
 #pragma unroll
             for (int k = 0; k < N; ++k) Qs[idx * N + k] = v[k];
         }
+        // the step ratio from FP64 once per patch, not once per warp
+        if (threadIdx.x == 0) s_sc = tile_half_ratio<C>(__ldg(dt + i), __ldg(dx + i));
         __syncthreads();
 
         C acc[kMaxPerThread][N];
@@ -123,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_tile(BatchView b, const S *__restr
 
         // Update, store, eigenvalue of the new state.
         const double h = __ldg(dx + i);
-        const C sc = C(__ldg(dt + i) / (2.0 * h));
+        const C sc = s_sc;
         S *dst = qout + __ldg(b.elem_off + i);
         C lmax = C(0);
         bool bad = false;

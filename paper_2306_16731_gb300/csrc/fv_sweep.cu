@@ -146,6 +146,35 @@ template <> __device__ __forceinline__ double half_step_ratio<double>(double dt,
     return dt / (2.0 * h);
 }
 
+// Per-patch maximum eigenvalue and next time step; one lane per patch
+// writes.  Edges that are powers of two give P-aligned lane segments, which
+// reduce by xor shuffles (log2 P steps); other edges through shared memory.
+template <typename C>
+__device__ __forceinline__ void patch_lambda2(const SweepParams &sp, C lmax, int lane, int x, int P, bool active,
+                                              int i, double h, C *red)
+{
+    if ((P & (P - 1)) == 0) {
+        C m = lmax;
+        for (int o = P >> 1; o > 0; o >>= 1) m = fv_max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (active && x == 0 && (sp.lambda_out || sp.dt_next_out)) {
+            const double l = double(m);
+            if (sp.lambda_out) sp.lambda_out[i] = l;
+            if (sp.dt_next_out) sp.dt_next_out[i] = cfl_dt(sp.cfl, h, 2, l);
+        }
+        return;
+    }
+    red[lane] = lmax;
+    __syncwarp();
+    if (active && x == 0 && (sp.lambda_out || sp.dt_next_out)) {
+        C m = red[lane];
+        for (int j = 1; j < P; ++j) m = fv_max(m, red[lane + j]);
+        const double l = double(m);
+        if (sp.lambda_out) sp.lambda_out[i] = l;
+        if (sp.dt_next_out) sp.dt_next_out[i] = cfl_dt(sp.cfl, h, 2, l);
+    }
+    __syncwarp();
+}
+
 // Cheap running check of the new states: the minimum of density and
 // pressure must stay positive and the sum of eigenvalues finite (NaN and
 // infinity propagate through the sum).
@@ -341,16 +370,7 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
     }
 
     // per-patch maximum eigenvalue and next time step
-    red[lane] = lmax;
-    __syncwarp();
-    if (active && x == 0 && (sp.lambda_out || sp.dt_next_out)) {
-        C m = red[lane];
-        for (int j = 1; j < P; ++j) m = fv_max(m, red[lane + j]);
-        const double l = double(m);
-        if (sp.lambda_out) sp.lambda_out[i] = l;
-        if (sp.dt_next_out) sp.dt_next_out[i] = cfl_dt(sp.cfl, h, 2, l);
-    }
-    __syncwarp();
+    patch_lambda2(sp, lmax, lane, x, P, active, i, h, red);
 }
 
 
@@ -454,23 +474,6 @@ __device__ __forceinline__ void boundary_face2(const C (&qL)[4], const C (&qR)[4
     store_volume<N>(hvol_slot, side ? qR : qL);
 }
 
-// Per-patch maximum eigenvalue and next time step (lanes of a patch slot
-// reduce through shared memory; one lane per patch writes).
-template <typename C>
-__device__ __forceinline__ void patch_lambda2(const SweepParams &sp, C lmax, int lane, int x, int P, bool active,
-                                              int i, double h, C *red)
-{
-    red[lane] = lmax;
-    __syncwarp();
-    if (active && x == 0 && (sp.lambda_out || sp.dt_next_out)) {
-        C m = red[lane];
-        for (int j = 1; j < P; ++j) m = fv_max(m, red[lane + j]);
-        const double l = double(m);
-        if (sp.lambda_out) sp.lambda_out[i] = l;
-        if (sp.dt_next_out) sp.dt_next_out[i] = cfl_dt(sp.cfl, h, 2, l);
-    }
-    __syncwarp();
-}
 
 // Compile-time edge P (32/P patches per warp): rows stream through a
 // per-warp shared-memory ring of R rows filled by cp.async, R-1 rows ahead
@@ -586,22 +589,13 @@ __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem
     }
     cp_async_wait<0>();
 
-    red[lane] = lmax;
-    __syncwarp();
-    if (active && x == 0 && (sp.lambda_out || sp.dt_next_out)) {
-        C m = red[lane];
-#pragma unroll
-        for (int j = 1; j < P; ++j) m = fv_max(m, red[lane + j]);
-        const double l = double(m);
-        if (sp.lambda_out) sp.lambda_out[i] = l;
-        if (sp.dt_next_out) sp.dt_next_out[i] = cfl_dt(sp.cfl, h, 2, l);
-    }
-    __syncwarp();
+    patch_lambda2(sp, lmax, lane, x, P, active, i, h, red);
 }
 
 // One launch per patch-size class: P > 0 selects the compile-time-edge
 // sweep, P == 0 the runtime-edge one.  Items [item_begin, item_begin +
 // num_items) of the sorted work list belong to the class.
+
 template <typename S, int P>
 __global__ void __launch_bounds__(FV_SWEEP_MAXT, FV_SWEEP_MINB) k_sweep2d(SweepParams sp)
 {

@@ -632,6 +632,25 @@ def other_workloads(dev, stream, flush_l2, steps):
         b.status()
         return tot / k
 
+    def graph_steps(b, qs, dx, lam, dts, nsteps, cfl):
+        """Per-step time of an nsteps CFL-chained run captured as one CUDA
+        graph (first replay captures; median of 5 timed replays).  The state
+        is not flushed between the steps of a run: for batches below the L2
+        size this is the L2-warm multi-step number beside the flushed one."""
+        b.run(qs[0], qs[1], dx, dts[0], dts[1], lam, nsteps, cfl, True)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(5):
+            flush_l2()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            b.run(qs[0], qs[1], dx, dts[0], dts[1], lam, nsteps, cfl, True)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            times.append(g0.elapsed_time(g1) / nsteps)
+        b.status()
+        return float(np.median(times))
+
     def bytes_per_volume(w, es):
         p = w.patch_size.astype(np.float64)
         N = w.dim + 2
@@ -665,9 +684,12 @@ def other_workloads(dev, stream, flush_l2, steps):
         del scratch
         ms = single_steps(b, qs, dx, lam, dts, k, w3.cfl)
         bpv = bytes_per_volume(w3, es)
+        gms = graph_steps(b, qs, dx, lam, dts, w3.steps, w3.cfl)
         res[name] = {"value": w3.interior_volumes / (ms / 1e3), "ms_per_step": ms,
                      "bytes_per_volume": bpv, "achieved_gbs": w3.interior_volumes * bpv / (ms / 1e3) / 1e9,
                      "roofline_frac": w3.interior_volumes * bpv / (ms / 1e3) / 1e9 / peak,
+                     "value_graph_%dsteps_l2warm" % w3.steps: w3.interior_volumes / (gms / 1e3),
+                     "ms_per_step_graph_l2warm": gms,
                      "kernel": b.describe()}
         b.close()
         final_sample(name, w3, prec, w3.steps, 16, 31)

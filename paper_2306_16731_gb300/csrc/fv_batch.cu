@@ -788,7 +788,14 @@ int fv_batch_launches_per_update(const fv_batch_t *b)
     case FV_FORM_CASCADE: return 5;
     case FV_FORM_TILE: return 1;
     case FV_FORM_TASKGRAPH: return b->T * (2 * b->dim + 3);   // kernel nodes of the one graph launch
-    default: return b->plan.num_classes;   // one launch per patch-size class (neighbours read in-kernel)
+    default: {  // 2D edges 4, 8, 16, 32: one launch over every size class; else one per class
+        bool compiled = b->fused_kernel == fv::FUSED_SWEEP2D;
+        for (int c = 0; c < b->plan.num_classes; ++c) {
+            const int p = b->plan.class_p[c];
+            compiled = compiled && (p == 4 || p == 8 || p == 16 || p == 32);
+        }
+        return compiled ? 1 : b->plan.num_classes;
+    }
     }
 }
 

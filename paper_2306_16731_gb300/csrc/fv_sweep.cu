@@ -592,9 +592,12 @@ __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem
     patch_lambda2(sp, lmax, lane, x, P, active, i, h, red);
 }
 
-// One launch per patch-size class: P > 0 selects the compile-time-edge
-// sweep, P == 0 the runtime-edge one.  Items [item_begin, item_begin +
-// num_items) of the sorted work list belong to the class.
+// P > 0 selects the compile-time-edge sweep for one patch-size class, P == 0
+// the runtime-edge one; P < 0 takes the items of every class in one launch
+// when all edges are 4, 8, 16 or 32 (each item dispatched on its edge; items
+// sorted largest patches first, so persistent warps end on the small ones).
+// Items [item_begin, item_begin + num_items) of the sorted work list belong
+// to the launch.
 
 template <typename S, int P>
 __global__ void __launch_bounds__(FV_SWEEP_MAXT, FV_SWEEP_MINB) k_sweep2d(SweepParams sp)
@@ -619,8 +622,18 @@ __global__ void __launch_bounds__(FV_SWEEP_MAXT, FV_SWEEP_MINB) k_sweep2d(SweepP
         } else {
             it = sp.items[item];
         }
-        if (P > 0) sweep2d_tpl<S, C, (P > 0 ? P : 4)>(sp, it, lane, bface, hvol, red, ring, hl);
-        else sweep2d_item<S, C>(sp, it, lane, bface, hvol, red, hl);
+        if (P > 0) {
+            sweep2d_tpl<S, C, (P > 0 ? P : 4)>(sp, it, lane, bface, hvol, red, ring, hl);
+        } else if (P < 0) {                 // every size class in one launch
+            switch (it.p) {
+            case 4: sweep2d_tpl<S, C, 4>(sp, it, lane, bface, hvol, red, ring, hl); break;
+            case 8: sweep2d_tpl<S, C, 8>(sp, it, lane, bface, hvol, red, ring, hl); break;
+            case 16: sweep2d_tpl<S, C, 16>(sp, it, lane, bface, hvol, red, ring, hl); break;
+            default: sweep2d_tpl<S, C, 32>(sp, it, lane, bface, hvol, red, ring, hl); break;   // 32
+            }
+        } else {
+            sweep2d_item<S, C>(sp, it, lane, bface, hvol, red, hl);
+        }
     };
     if (!sp.persistent) {
         const int item = blockIdx.x * wpb + warp;
@@ -953,6 +966,21 @@ cudaError_t launch_fused_update(const BatchView &b, int precision, const StepArg
     if (wpb < 1) wpb = 1;
     if (wpb > kMaxWarpsPerBlock) wpb = kMaxWarpsPerBlock;
     sp.persistent = plan.shape.blocks_per_sm != 0;      // -1 and -2 are persistent too
+    bool compiled_edges = true;
+    for (int c = 0; c < plan.num_classes; ++c) {
+        const int p = plan.class_p[c];
+        compiled_edges = compiled_edges && (p == 4 || p == 8 || p == 16 || p == 32);
+    }
+    if (plan.num_classes > 1 && compiled_edges) {
+        // uneven batch of compiled edges: one launch over all items
+        sp.item_begin = plan.class_begin[0];
+        sp.num_items = plan.class_end[plan.num_classes - 1] - plan.class_begin[0];
+        sp.counter = plan.work_counter;
+        const int bps = plan.shape.blocks_per_sm == -2 ? -1 : plan.shape.blocks_per_sm;
+        if (precision == PREC_F64) return launch_class<double, -1>(sp, wpb, bps, st);
+        if (precision == PREC_F32) return launch_class<float, -1>(sp, wpb, bps, st);
+        return launch_class<__nv_bfloat16, -1>(sp, wpb, bps, st);
+    }
     for (int c = 0; c < plan.num_classes; ++c) {
         sp.item_begin = plan.class_begin[c];
         sp.num_items = plan.class_end[c] - plan.class_begin[c];

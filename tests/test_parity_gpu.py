@@ -1112,3 +1112,40 @@ def test_host_update_graph_replays_new_contents_and_falls_back_for_pageable_buff
         assert all(np.array_equal(g, r) for g, r in zip(got, ref)), (pin, change)
         assert np.array_equal(gl, ref_lam), (pin, change)
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uneven_2d_batch_runs_as_one_launch_when_edges_are_compiled(precision):
+    """An uneven 2D batch whose edges are all 4, 8, 16 or 32 is updated by one
+    launch over every size class (items dispatched on their edge); with a
+    runtime edge among them it falls back to one launch per class.  Both
+    match the oracle, fixed and periodic, and every launch shape gives the
+    same bits."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    rng = np.random.default_rng(77)
+    for sizes, launches in ((rng.choice([4, 8, 16, 32], 900), 1), (np.r_[rng.choice([4, 8, 16], 300), [5] * 7], 4)):
+        for halo in (inputs.FIXED, inputs.PERIODIC):
+            w = inputs.uniform_batch(2, sizes, seed=170 + halo, dx=np.linspace(0.05, 0.2, len(sizes)),
+                                     halo_mode=halo, dtype=np.float32 if precision == 1 else np.float64)
+            T = w.num_patches
+            results = []
+            for shape in ((4, 0), (2, -1), (8, 1)):
+                b = fb.FVBatch(2, w.patch_size, precision=precision, halo_mode=halo)
+                b.set_launch_shape(*shape)
+                assert b.launches_per_update() == launches
+                qa = to_device(w.Q0, precision)
+                qb = qa.clone()
+                dx = torch.tensor(w.dx, device="cuda")
+                dt = torch.full((T,), 1e-3, dtype=torch.float64, device="cuda")
+                lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+                b.update(qa, qb, dx, dt, lam, None, 0.4)
+                b.status()
+                results.append((qb.to(torch.float64).cpu().numpy(), lam.cpu().numpy()))
+                b.close()
+            for q, l in results[1:]:
+                assert np.array_equal(q, results[0][0]) and np.array_equal(l, results[0][1])
+            ref, lam_ref = oracle.batch_step(2, w.patch_size, w.dx, [1e-3] * T, initial_fp64(w.Q0, precision),
+                                             halo_mode=halo)
+            assert batch_rel_linf(results[0][0], ref, 2, w.patch_size) < TOL[precision]
+            assert np.max(np.abs(results[0][1] - lam_ref) / lam_ref) < TOL[precision]

@@ -599,8 +599,17 @@ __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem
 // Items [item_begin, item_begin + num_items) of the sorted work list belong
 // to the launch.
 
+// The launch over every size class inlines four sweeps and would take 104
+// registers in FP32; it is held to 64 (two full blocks per SM, 32 warps),
+// which measured 11% faster on a 50,000-patch uneven batch.
 template <typename S, int P>
-__global__ void __launch_bounds__(FV_SWEEP_MAXT, FV_SWEEP_MINB) k_sweep2d(SweepParams sp)
+constexpr int sweep2d_min_blocks()
+{
+    return (P < 0 && sizeof(S) < 8) ? 2 : FV_SWEEP_MINB;
+}
+
+template <typename S, int P>
+__global__ void __launch_bounds__(FV_SWEEP_MAXT, (sweep2d_min_blocks<S, P>())) k_sweep2d(SweepParams sp)
 {
     using C = typename StorageTraits<S>::Compute;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -11,9 +11,8 @@ One benchmark "step" is one time step of the whole batch: one call of
 face fluxes, update, per-patch eigenvalue maximum and next CFL time step).
 The headline value is the fused FP32 form; the FP64 fused and the plain FP64
 loop-cascade forms are timed beside it.  L2 is flushed (256 MiB write, then a
-256 MiB read)
-before every timed step and each step is timed alone with CUDA events on the
-launching stream.
+256 MiB read) before every timed step and each step is timed alone with CUDA
+events on the launching stream.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle instead (the reference arm of this project).

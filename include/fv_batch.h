@@ -96,7 +96,8 @@ enum {
 
 /* Kernel realisation (Sec. 3). */
 enum {
-    FV_FORM_FUSED = 0,      /* default: one fused launch per step (warp-level sweep kernels) */
+    FV_FORM_FUSED = 0,      /* default: every step fused (warp-level sweep kernels); one persistent launch for a 2D
+                               batch whose edges are all 4, 8, 16 or 32, else one launch per patch-size class */
     FV_FORM_CASCADE = 1,    /* one launch per algorithmic step over all volumes, intermediates in device memory (batched realisation) */
     FV_FORM_TILE = 2,       /* one thread block per patch staged in shared memory (patch-wise realisation) */
     FV_FORM_TASKGRAPH = 3   /* task-graph realisation (Sec. 3): one CUDA graph per update whose nodes are the
@@ -343,7 +344,9 @@ size_t fv_batch_scratch_bytes(const fv_batch_t *b);
 int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len);
 
 /* Number of kernel launches one fv_patch_batch_update call makes with the
- * current form and arguments (lambda/dt outputs present). */
+ * current form and arguments (lambda/dt outputs present): for the fused form
+ * 1 when the batch is 2D with edges 4, 8, 16 and 32 only, else one per
+ * patch-size class. */
 int fv_batch_launches_per_update(const fv_batch_t *b);
 
 /*

@@ -388,13 +388,14 @@ cudaError_t launch3(const Sweep3Params &sp, int chunk, cudaStream_t st, int prec
 
 // ---------------------------------------------------------------------------
 // Edge lengths that are multiples of 8: one warp per 8 x 8 column block of a
-// patch (the patch's (p/8)^2 warps share only the plane ring), two columns
-// per lane: lane = (x, yb) with x = lane % 8, yb = lane / 8, owning rows yb
-// (cell A) and yb + 4 (cell B) of the block.
+// patch (the patch's (p/8)^2 warps share only the plane ring), two volumes
+// per lane: lane = (x, yb) with x = lane % 8, yb = lane / 8, owning rows 2yb
+// (cell A) and 2yb + 1 (cell B) of column x of the block.
 //   * x faces: the right neighbour's Q, F_x, lambda_x by shuffle (lane + 1),
 //     the left face as the left lane's right face (lane - 1);
-//   * y faces: the upper neighbour by shuffle (lane + 8), cell A of the top
-//     lane row taking the own cell B; lower faces by shuffle back;
+//   * y faces: the face between the lane's two rows in registers; the face
+//     above row 2yb + 1 with cell A of lane + 8; the face below row 2yb is
+//     the upper face of lane - 8's cell B, by one shuffle back;
 //   * the 32 faces between the block and its ring (patch halo or the
 //     neighbouring block's volumes) are computed first, one per lane, into
 //     shared memory, so no lane does extra face work inside the sweep;
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
 
     const int x0 = (warp % nb) * 8, y0 = (warp / nb) * 8;
     const int x = lane & 7, yb = lane >> 3;
-    const int gx = x0 + x, gyA = y0 + yb, gyB = y0 + yb + 4;
+    const int gx = x0 + x, gyA = y0 + 2 * yb, gyB = gyA + 1;
     const int cellA = (gyA + 1) * E + (gx + 1), cellB = (gyB + 1) * E + (gx + 1);
 
     // this lane's ring volume and the interior volume next to it
@@ -594,9 +595,9 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
             // every lane reads one edge entry per row (side 1 for column 7,
             // side 0 otherwise), so the edge columns cost one set of loads
             C eA[N], eB[N];
-            const int ex = (x == 7 ? 8 : 0) + yb;
+            const int ex = (x == 7 ? 8 : 0) + 2 * yb;
 #pragma unroll
-            for (int k = 0; k < N; ++k) { eA[k] = bf[ex * N + k]; eB[k] = bf[(ex + 4) * N + k]; }
+            for (int k = 0; k < N; ++k) { eA[k] = bf[ex * N + k]; eB[k] = bf[(ex + 1) * N + k]; }
             if (x == 7) {
 #pragma unroll
                 for (int k = 0; k < N; ++k) { FrA[k] = eA[k]; FrB[k] = eB[k]; }
@@ -610,34 +611,20 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
 #pragma unroll
             for (int k = 0; k < N; ++k) { dA[k] = FrA[k] - FlA[k]; dB[k] = FrB[k] - FlB[k]; }
         }
-        // y faces
+        // y faces: rows 2yb | 2yb+1 inside the lane; row 2yb+1 | 2yb+2 with
+        // the A row of lane + 8 (the block's top edge face for yb = 3); the
+        // face below row 2yb is the upper face of row 2yb-1, B of lane - 8
+        // (the block's bottom edge face for yb = 0)
         {
-            C FyA[N], FyB[N], nq[N], nF[N], FuA[N], FuB[N], FdA[N], FdB[N], t[N];
+            C FyA[N], FyB[N], nq[N], nF[N], FuA[N], FuB[N], FdA[N];
             flux<3>(qA, sA, 1, FyA);
             flux<3>(qB, sB, 1, FyB);
             const C lyA = eigenvalue<3>(sA, 1), lyB = eigenvalue<3>(sB, 1);
             const bool top = yb == 3, bottom = yb == 0;
-            // upper face of A: neighbour lane + 8 (A); for the top lane row
-            // (row 3) it is row 4, the B of lane - 24
+            rusanov2<N>(qA, qB, FyA, FyB, lyA, lyB, FuA);
             shfl_vec<N>(nq, qA, 8, true);
             shfl_vec<N>(nF, FyA, 8, true);
-            C nl = __shfl_down_sync(0xffffffffu, lyA, 8);
-            {
-                C bq[N], bF[N];
-                shfl_vec<N>(bq, qB, 24, false);
-                shfl_vec<N>(bF, FyB, 24, false);
-                const C bl = __shfl_up_sync(0xffffffffu, lyB, 24);
-                if (top) {
-#pragma unroll
-                    for (int k = 0; k < N; ++k) { nq[k] = bq[k]; nF[k] = bF[k]; }
-                    nl = bl;
-                }
-            }
-            rusanov2<N>(qA, nq, FyA, nF, lyA, nl, FuA);
-            // upper face of B: neighbour lane + 8 (B), or the block's upper boundary
-            shfl_vec<N>(nq, qB, 8, true);
-            shfl_vec<N>(nF, FyB, 8, true);
-            nl = __shfl_down_sync(0xffffffffu, lyB, 8);
+            const C nl = __shfl_down_sync(0xffffffffu, lyA, 8);
             rusanov2<N>(qB, nq, FyB, nF, lyB, nl, FuB);
             C ey[N];                                          // side 3 for the top row, side 2 otherwise
 #pragma unroll
@@ -646,17 +633,13 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
 #pragma unroll
                 for (int k = 0; k < N; ++k) FuB[k] = ey[k];
             }
-            // lower faces: the lower lane's upper faces; row 4 (B of the bottom
-            // lane row) takes the upper face of row 3 (A of lane + 24)
-            shfl_vec<N>(FdA, FuA, 8, false);
-            shfl_vec<N>(FdB, FuB, 8, false);
-            shfl_vec<N>(t, FuA, 24, true);
+            shfl_vec<N>(FdA, FuB, 8, false);
             if (bottom) {
 #pragma unroll
-                for (int k = 0; k < N; ++k) { FdA[k] = ey[k]; FdB[k] = t[k]; }
+                for (int k = 0; k < N; ++k) FdA[k] = ey[k];
             }
 #pragma unroll
-            for (int k = 0; k < N; ++k) { dA[k] += FuA[k] - FdA[k]; dB[k] += FuB[k] - FdB[k]; }
+            for (int k = 0; k < N; ++k) { dA[k] += FuA[k] - FdA[k]; dB[k] += FuB[k] - FuA[k]; }
         }
         __syncwarp();                                        // boundary faces consumed
     }

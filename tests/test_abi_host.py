@@ -86,3 +86,25 @@ def test_null_batch_is_rejected_or_ignored(lib):
     assert lib.fv_max_eigenvalue(None, None, None) == -1
     assert lib.fv_batch_status(None) == -1
     assert lib.fv_batch_state_elems(None) == 0
+
+
+def _declared_arities():
+    """Parameter count of every fv_* declaration in include/*.h."""
+    arity = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(fv_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+            params = m.group(2).strip()
+            arity[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return arity
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """The ctypes signatures the binding registers have as many arguments as
+    the header's declarations (catches a parameter added on one side only)."""
+    arity = _declared_arities()
+    assert set(arity) >= set(_declared_functions()) - {"fv_last_error"}
+    registered = {n: getattr(lib, n).argtypes for n in arity}
+    assert all(v is not None for v in registered.values()), [n for n, v in registered.items() if v is None]
+    mismatched = {n: (k, len(registered[n])) for n, k in arity.items() if len(registered[n]) != k}
+    assert mismatched == {}

@@ -51,7 +51,7 @@ def parse_args():
                     help="skip the secondary 3D / uneven workload lines")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--profile", choices=["fused_f32", "fused_f64", "cascade_f64", "tile_f32",
-                                          "fused3d_f32", "fused3d16_f32", "fused3dper_f32"],
+                                          "fused3d_f32", "fused3d16_f32", "fused3dper_f32", "uneven_f32"],
                     default=None, help="no timing: run a few launches of one form for ncu")
     ap.add_argument("--patches", type=int, default=None,
                     help="with --profile: batch size (default 65536, state larger than L2)")
@@ -882,6 +882,11 @@ def run_profile(args):
         T = args.patches or (4096 if p3 == 16 else 16384)
         halo = inputs.PERIODIC if form_name == "fused3dper" else inputs.FIXED
         w = inputs.uniform_batch(3, [p3] * T, seed=3, dx=0.01, dtype=np.float32, halo_mode=halo)
+        form_name = "fused"
+    elif form_name == "uneven":
+        # the 50,000-patch uneven batch (edges 4..32, dx = 3^-k), one launch per step
+        w = inputs.config(4, dtype=np.float32, num_patches=args.patches)
+        T = w.num_patches
         form_name = "fused"
     else:
         T = args.patches or 65536

@@ -61,7 +61,7 @@ enum {
     FV_EINVAL = -1,         /* bad argument (size, pointer, alias, mode) */
     FV_ENOMEM = -2,         /* host or device allocation failed */
     FV_ECUDA = -3,          /* a CUDA runtime call failed */
-    FV_EUNSUPPORTED = -4,   /* valid request no kernel of this build covers */
+    FV_EUNSUPPORTED = -4,   /* valid request that no kernel of the library covers */
     FV_ENONPHYSICAL = -5,   /* device met rho <= 0, p <= 0 or a non-finite eigenvalue */
     FV_ETIMEOUT = -6        /* a kernel's bounded wait for its own copy ran out (1 s); that
                                update's results are invalid, the context stays usable */

@@ -387,7 +387,7 @@ static int create_batch(fv_batch_t **out, int pde, int dim, int num_patches, con
     b->plan.shape.warps_per_block = 4;
     b->plan.shape.blocks_per_sm = 0;
 
-    // Default form: fused sweep if this build covers the shapes, else the
+    // Default form: fused sweep if the library has a kernel for the shapes, else the
     // patch-wise tile kernel, else the loop cascade.  Other PDEs than Euler
     // run on the generic patch-wise kernel only.
     if (pde != FV_PDE_EULER) {

@@ -29,3 +29,18 @@ def test_reference_arm_prints_the_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_algorithmic_bytes_match_the_stated_per_volume_figures():
+    """The roofline's algorithmic bytes per volume: every needed volume read
+    once (interior plus the 2d face-halo layers; periodic halos rebuilt on
+    chip) and the interior written once."""
+    import bench
+    f = bench.algorithmic_bytes_per_volume
+    assert f(2, 16, 4, 4) == 36.0                    # 2D 16^2 FP32
+    assert f(2, 16, 4, 8) == 72.0                    # 2D 16^2 FP64
+    assert f(3, 8, 5, 4, periodic=True) == 40.0      # 3D 8^3 periodic FP32
+    assert f(3, 8, 5, 2, periodic=True) == 20.0      # 3D 8^3 periodic BF16 storage
+    assert f(3, 16, 5, 4) == 47.5                    # 3D 16^3 FP32
+    # by hand for a small fixed patch: 3^2 interior + 4 x 3 face halo read, 3^2 written
+    assert f(2, 3, 4, 8) == 4 * 8 * (9 + 12 + 9) / 9

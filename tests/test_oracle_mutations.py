@@ -39,6 +39,12 @@ MUTANTS = {
     "periodic_wrap_swapped": ("src[axis] = idx[axis] == -1 ? p - 1 : 0;",
                               "src[axis] = idx[axis] == -1 ? 0 : p - 1;"),
     "cfl_without_dimension": ("((double)dim * lambda[i])", "(lambda[i])"),
+    "totals_include_x_halo": ("for (int ii = 0; ii < P; ++ii) {\n                    const double *c = Q + off[i]",
+                              "for (int ii = -1; ii <= P; ++ii) {\n                    const double *c = Q + off[i]"),
+    "totals_include_y_halo": ("for (int j = 0; j < P; ++j)\n                for (int ii = 0; ii < P; ++ii) {\n                    const double *c",
+                              "for (int j = -1; j < P; ++j)\n                for (int ii = 0; ii < P; ++ii) {\n                    const double *c"),
+    "totals_skip_last_z_plane": ("int kmax = dim == 3 ? P - 1 : 0;", "int kmax = dim == 3 ? P - 2 : 0;"),
+    "totals_wrong_patch_offset": ("const double *c = Q + off[i] + cell_index", "const double *c = Q + off[0] + cell_index"),
     "max_eigenvalue_over_first_direction_only": ("for (int n = 0; n < dim; ++n) {\n                    double l",
                                                  "for (int n = 0; n < 1; ++n) {\n                    double l"),
 }
@@ -64,6 +70,9 @@ def _pin_checks():
     c.append(("hand_worked", pins.test_hand_worked_single_volume))
     c.append(("eigenvalue_cfl", pins.test_max_eigenvalue_and_cfl_closed_form))
     c.append(("fixed_halo", pins.test_fixed_halo_is_copied_unchanged))
+    for dim in (2, 3):
+        c.append(("totals_closed_form_%d" % dim, lambda dim=dim: pins.test_batch_totals_closed_form_exclude_halos(dim)))
+        c.append(("totals_interior_sums_%d" % dim, lambda dim=dim: pins.test_batch_totals_are_interior_sums(dim)))
     return c
 
 

@@ -404,3 +404,58 @@ def test_workloads_stay_physical(index, npatch):
 def patches_of(w, flat):
     from tests._helpers import patches_interior
     return patches_interior(flat, w.dim, w.patch_size)
+
+
+# ------------------------------------------------- conservation totals
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_batch_totals_closed_form_exclude_halos(dim):
+    """Per-patch totals of a ragged batch of constant patches: p_i^d copies of
+    the patch's state q_i summed, so exactly p_i^d q_i (the values have few
+    significant bits, so every partial sum is exact).  The halo volumes hold
+    a different value that would show in the totals if any were summed."""
+    sizes = [1, 3, 2, 5] if dim == 2 else [1, 3, 2, 4]
+    N = dim + 2
+    states = [np.array([1.5, -0.25, 0.75, 2.5, 0.125][:N]) * (i + 1) for i in range(len(sizes))]
+    parts = []
+    for p, q in zip(sizes, states):
+        a = np.full((p + 2,) * dim + (N,), 1.0e6)
+        a[(slice(1, -1),) * dim] = q
+        parts.append(a.reshape(-1))
+    tot = oracle.batch_totals(dim, sizes, np.concatenate(parts))
+    want = np.array([p ** dim * q for p, q in zip(sizes, states)])
+    assert np.array_equal(np.asarray(tot).reshape(len(sizes), N), want)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_batch_totals_are_interior_sums(dim):
+    """Random ragged patches: the totals equal a brute-force sum over each
+    patch's interior slice, and changing one halo volume (of any face) or
+    one interior volume of the last plane changes exactly what it should."""
+    rng = np.random.default_rng(71 + dim)
+    sizes = [3, 5, 2] if dim == 3 else [4, 7, 1, 6]
+    N = dim + 2
+    pats = [random_patch(rng, dim, p) for p in sizes]
+    flat = np.concatenate([q.reshape(-1) for q in pats])
+    tot = np.asarray(oracle.batch_totals(dim, sizes, flat)).reshape(len(sizes), N)
+    for i, q in enumerate(pats):
+        brute = interior(q, dim).reshape(-1, N).sum(axis=0)
+        assert np.allclose(tot[i], brute, rtol=1e-13, atol=0)
+    # halo volumes on every face do not count
+    for axis in range(dim):
+        for side in (0, -1):
+            mod = [q.copy() for q in pats]
+            idx = [slice(1, -1)] * dim
+            idx[axis] = side
+            mod[0][tuple(idx)] += 100.0
+            t2 = np.asarray(oracle.batch_totals(dim, sizes, np.concatenate([q.reshape(-1) for q in mod])))
+            assert np.array_equal(t2.reshape(len(sizes), N), tot)
+    # the last interior plane along the slowest axis does count
+    mod = [q.copy() for q in pats]
+    idx = [slice(1, -1)] * dim
+    idx[0] = -2
+    mod[-1][tuple(idx)] += 1.0
+    t3 = np.asarray(oracle.batch_totals(dim, sizes, np.concatenate([q.reshape(-1) for q in mod]))).reshape(len(sizes), N)
+    p = sizes[-1]
+    assert np.allclose(t3[-1] - tot[-1], p ** (dim - 1), rtol=1e-12)
+    assert np.array_equal(t3[:-1], tot[:-1])

@@ -367,7 +367,9 @@ int fv_batch_launches_per_update(const fv_batch_t *b);
  * process exits; a batch that needs more (about 1,300 two-dimensional
  * 16 x 16 patches in FP64, 2,700 in FP32) is rejected with FV_EINVAL and
  * nothing is launched.  The first call on a device looks up the array's
- * device address (make it before any stream capture).  All calls share the
+ * device address (make it before any stream capture); a call with
+ * num_patches = 0 on that device does this lookup and nothing else, so it
+ * serves as a cheap first call (no buffers needed).  All calls share the
  * array: calls whose work overlaps on the GPU race, so serialise them.
  * Non-physical states are not reported by this entry point (see the
  * returned eigenvalues instead).  Returns FV_OK or an FV_E* code.

@@ -17,9 +17,11 @@
 // stand-in), so the first call on each device, with that device current,
 // asks the runtime for the array's device address (cudaGetSymbolAddress)
 // and caches it; that first call should therefore come before any stream
-// capture.  Every call shares the one array: calls whose work overlaps on
-// the GPU (different streams, or different host threads on one device)
-// race and corrupt each other's intermediates; serialise them.
+// capture.  A call with num_patches == 0 (argument checks passed) does that
+// lookup and nothing else, so it primes a device cheaply.  Every call
+// shares the one array: calls whose work overlaps on the GPU (different
+// streams, or different host threads on one device) race and corrupt each
+// other's intermediates; serialise them.
 #include <algorithm>
 #include <mutex>
 
@@ -75,6 +77,27 @@ extern "C" int fv_patch_batch_update_noalloc(int dim, int num_patches, int patch
     if (!(gamma > 1.0) || !(gamma < 1e300)) return noalloc_fail(FV_EINVAL, "gamma must be finite and > 1");
     if (patch_size < 1 || patch_size > (dim == 2 ? 1024 : 128))
         return noalloc_fail(FV_EINVAL, "patch edge length out of range");
+    // the scratch array's device address on the current device: looked up
+    // by the first call there (a call with num_patches == 0 does only this)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(FV_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(FV_EUNSUPPORTED, "device index beyond 63");
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_symbol_mu);
+        if (!g_symbol_addr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return noalloc_fail(FV_ECUDA, e != cudaSuccess ? cudaGetErrorString(e)
+                                                               : "no device address for the scratch array");
+            }
+            g_symbol_addr[dev] = ptr;
+        }
+        base = static_cast<unsigned char *>(g_symbol_addr[dev]);
+    }
     if (num_patches == 0) return FV_OK;
     if (!Q_in || !Q_out || !dx || !dt) return noalloc_fail(FV_EINVAL, "NULL state, dx or dt pointer");
     if ((reinterpret_cast<uintptr_t>(Q_in) | reinterpret_cast<uintptr_t>(Q_out)) & 15u)
@@ -113,26 +136,6 @@ extern "C" int fv_patch_batch_update_noalloc(int dim, int num_patches, int patch
         uintptr_t a = reinterpret_cast<uintptr_t>(Q_in), b = reinterpret_cast<uintptr_t>(Q_out);
         if (a < b + state_bytes && b < a + state_bytes)
             return noalloc_fail(FV_EINVAL, "Q_in and Q_out overlap (in-place update is not allowed)");
-    }
-
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(FV_ECUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(FV_EUNSUPPORTED, "device index beyond 63");
-    unsigned char *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_symbol_mu);
-        if (!g_symbol_addr[dev]) {
-            void *ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess || !ptr) {
-                cudaGetLastError();
-                return noalloc_fail(FV_ECUDA, e != cudaSuccess ? cudaGetErrorString(e)
-                                                               : "no device address for the scratch array");
-            }
-            g_symbol_addr[dev] = ptr;
-        }
-        base = static_cast<unsigned char *>(g_symbol_addr[dev]);
     }
 
     v.elem_off = reinterpret_cast<const int64_t *>(base + off_elem);

@@ -529,6 +529,11 @@ def test_host_state_update_matches_device_update(dim, sizes, precision, halo):
             continue
         assert all(np.array_equal(g, r) for g, r in zip(got, ref)), chunks
         assert np.array_equal(hl.numpy(), lam.cpu().numpy()) and np.array_equal(hd.numpy(), dtn.cpu().numpy())
+    # and the host path's result is the oracle's step from the same start
+    oref, olam = oracle.batch_step(dim, w.patch_size, w.dx, [2e-3] * T, initial_fp64(w.Q0, precision),
+                                   halo_mode=halo)
+    assert batch_rel_linf(hout.to(torch.float64).numpy(), oref, dim, w.patch_size) <= TOL[precision]
+    assert np.max(np.abs(hl.numpy() - olam) / olam) <= TOL[precision]
     b.close()
 
 
@@ -679,6 +684,11 @@ def test_taskgraph_form_is_bitwise_the_batched_cascade(dim, sizes, halo, precisi
     assert "form=taskgraph" in got[3]
     for a, b in zip(got[:3], ref[:3]):
         assert np.array_equal(a, b)
+    # and it is the oracle's step (dt = 1e-3 for every patch)
+    oref, olam = oracle.batch_step(dim, w.patch_size, w.dx, [1e-3] * w.num_patches, initial_fp64(w.Q0, precision),
+                                   halo_mode=halo)
+    assert batch_rel_linf(got[0], oref, dim, w.patch_size) <= TOL[precision]
+    assert np.max(np.abs(got[1] - olam) / olam) <= TOL[precision]
 
 
 def test_taskgraph_form_multi_step_run_equals_cascade():
@@ -688,6 +698,9 @@ def test_taskgraph_form_multi_step_run_equals_cascade():
     a = gpu_run(w, 0, FORMS["cascade"], 5)
     b = gpu_run(w, 0, 3, 5, use_graph=True)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    ref, lam_ref, dt_ref = _oracle(w, 0, 5)
+    assert batch_rel_linf(b[0], ref, 2, w.patch_size) <= TOL[0]
+    assert np.max(np.abs(b[1] - lam_ref) / lam_ref) <= TOL[0] and np.max(np.abs(b[2] - dt_ref) / dt_ref) <= TOL[0]
 
 
 # ------------------------------------------------- generic PDE (Eq. 1): shallow water
@@ -858,6 +871,11 @@ def test_scattered_host_patches_match_the_device_update(dim, sizes, precision, h
     gi, ri = patches_interior(got, dim, w.patch_size), patches_interior(ref, dim, w.patch_size)
     for g_, r_ in zip(gi, ri):
         assert np.array_equal(g_, r_)
+    # the gathered update is the oracle's step
+    q0 = initial_fp64(w.Q0, precision)
+    o1, ol1 = oracle.batch_step(dim, w.patch_size, w.dx, [1e-3] * T, q0, halo_mode=halo)
+    assert batch_rel_linf(got, o1, dim, w.patch_size) <= TOL[precision]
+    assert np.max(np.abs(lam.numpy() - ol1) / ol1) <= TOL[precision]
     assert np.array_equal(lam.numpy(), rl.cpu().numpy()) and np.array_equal(dtn.numpy(), rn.cpu().numpy())
     # halo volumes of the output patches keep the sentinel
     for t, p in zip(outs, w.patch_size):
@@ -882,6 +900,9 @@ def test_scattered_host_patches_match_the_device_update(dim, sizes, precision, h
     for g_, r_ in zip(patches_interior(got2, dim, w.patch_size),
                       patches_interior(qa2.to(torch.float64).cpu().numpy(), dim, w.patch_size)):
         assert np.array_equal(g_, r_)
+    # second step against the oracle's second step (fixed halos as given)
+    o2, _ = oracle.batch_step(dim, w.patch_size, w.dx, [1e-3] * T, o1, halo_mode=halo)
+    assert batch_rel_linf(got2, o2, dim, w.patch_size) <= 2 * TOL[precision]
     b.set_host_patches(None, None)
     b.close()
 

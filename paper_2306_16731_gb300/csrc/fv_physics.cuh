@@ -188,6 +188,85 @@ __device__ __forceinline__ void rusanov2(const C (&qL)[N], const C (&qR)[N], con
     for (int k = 0; k < N; ++k) Fh[k] = (FL[k] + FR[k]) - lam * (qR[k] - qL[k]);
 }
 
+// ------------------------------------------- 2D FP32: one rounding per step
+//
+// The FP32 2D microkernels spell every operation out (round-to-nearest
+// add/sub/mul/fma, the approximate reciprocal and square root of the
+// fast-math FP32 build) in a fixed order: which multiplies and adds become
+// one fma is then fixed by the source, not left to the compiler, so every
+// 2D FP32 kernel rounds a volume's arithmetic at the same places.
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <>
+__device__ __forceinline__ Prim<2, float> primitives<2, float>(const float (&q)[4], Gas<float> g)
+{
+    Prim<2, float> s;
+    const float r = rcp_approx(q[0]);
+    s.u[0] = __fmul_rn(q[1], r);
+    s.u[1] = __fmul_rn(q[2], r);
+    const float kin = __fmaf_rn(q[2], s.u[1], __fmul_rn(q[1], s.u[0]));
+    s.p = __fmul_rn(g.gm1, __fmaf_rn(-0.5f, kin, q[3]));
+    s.c = sqrt_approx(__fmul_rn(__fmul_rn(g.gamma, s.p), r));
+    return s;
+}
+
+template <>
+__device__ __forceinline__ float eigenvalue<2, float>(const Prim<2, float> &s, int n)
+{
+    return __fadd_rn(fabsf(s.u[n]), s.c);
+}
+
+template <>
+__device__ __forceinline__ float max_eigenvalue<2, float>(const Prim<2, float> &s)
+{
+    return __fadd_rn(fmaxf(fabsf(s.u[0]), fabsf(s.u[1])), s.c);
+}
+
+template <>
+__device__ __forceinline__ void flux<2, float>(const float (&q)[4], const Prim<2, float> &s, int n, float (&F)[4])
+{
+    const float un = s.u[n];
+    F[0] = q[1 + n];
+    F[1] = n == 0 ? __fmaf_rn(q[1], un, s.p) : __fmul_rn(q[1], un);
+    F[2] = n == 1 ? __fmaf_rn(q[2], un, s.p) : __fmul_rn(q[2], un);
+    F[3] = __fmul_rn(__fadd_rn(q[3], s.p), un);
+}
+
+template <>
+__device__ __forceinline__ void rusanov2<4, float>(const float (&qL)[4], const float (&qR)[4], const float (&FL)[4],
+                                                   const float (&FR)[4], float lamL, float lamR, float (&Fh)[4])
+{
+    const float nl = -fmaxf(lamL, lamR);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Fh[k] = __fmaf_rn(nl, __fsub_rn(qR[k], qL[k]), __fadd_rn(FL[k], FR[k]));
+}
+
+// Update of one unknown from the doubled face fluxes:
+// Q_new = Q - (dt/2h) (dFx + (2Fy_up - 2Fy_low)), the x difference first.
+template <typename C>
+__device__ __forceinline__ C update_2d(C q, C sc, C dfx, C fy_up, C fy_low)
+{
+    return q - sc * (dfx + (fy_up - fy_low));
+}
+template <>
+__device__ __forceinline__ float update_2d<float>(float q, float sc, float dfx, float fy_up, float fy_low)
+{
+    return __fmaf_rn(-sc, __fadd_rn(dfx, __fsub_rn(fy_up, fy_low)), q);
+}
+
 // Non-physical state test used by the error flag: rho <= 0, p <= 0 or a
 // non-finite eigenvalue (NaN compares false).
 template <typename C>

@@ -136,10 +136,30 @@ template <> __device__ __forceinline__ Gas<double> gas_of<double>(const SweepPar
 }
 
 // dt / (2h) in compute type (float arithmetic for float compute).
+// double -> float, rounded to nearest even, on the integer units: GB300's
+// FP64 unit, which also converts, is slow enough that a few conversions
+// per work item queue behind one another.  Normal float results only;
+// zero, subnormal, overflowing and non-finite inputs take the conversion
+// instruction.
+__device__ __forceinline__ float d2f_rn(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(b >> 32);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;      // float exponent field
+    if (e < 1 || e > 254) return float(v);
+    const unsigned long long m = b & 0xfffffffffffffull;            // 52 fraction bits
+    const unsigned long long rest = m & ((1ull << 29) - 1);          // the 29 bits rounded away
+    unsigned r = (unsigned)(m >> 29);
+    r += (rest > (1ull << 28) || (rest == (1ull << 28) && (r & 1u))) ? 1u : 0u;
+    // a carry out of the fraction moves into the exponent (and to infinity
+    // above the largest float), as rounding to nearest requires
+    return __uint_as_float((hi & 0x80000000u) | (((unsigned)e << 23) + r));
+}
+
 template <typename C> __device__ __forceinline__ C half_step_ratio(double dt, double h);
 template <> __device__ __forceinline__ float half_step_ratio<float>(double dt, double h)
 {
-    return __fdividef(float(dt), 2.0f * float(h));
+    return __fdividef(d2f_rn(dt), 2.0f * d2f_rn(h));
 }
 template <> __device__ __forceinline__ double half_step_ratio<double>(double dt, double h)
 {
@@ -200,9 +220,6 @@ __device__ __forceinline__ void store_row_volume(S *dst_row, const C (&qn)[N], b
 {
     if (!active) return;
     store_volume<N>(dst_row, qn);
-#ifdef FV_NO_HALO_WRITE
-    fixed = false;
-#endif
     if (fixed && x == 0) {
         C h[N];
         load_volume<N>(hv, h);
@@ -321,7 +338,7 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
         if (y > 0) {
             C qn[N];
 #pragma unroll
-            for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxp[k] + (Fyl[k] - Fylp[k]));
+            for (int k = 0; k < N; ++k) qn[k] = update_2d(qp[k], sc, dxp[k], Fyl[k], Fylp[k]);
             store_row_volume<N>(dst + (int64_t)y * RS, qn, active, !periodic, x, P, hv_row + (y - 1) * 2 * N);   // row y-1 lives at y
             Prim<2, C> t = primitives<2>(qn, g);
             const C l = max_eigenvalue<2>(t);
@@ -361,7 +378,7 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
         rusanov2<N>(qp, q0, Fyp, Fy, lyp, ly, Fyu);
         C qn[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxp[k] + (Fyu[k] - Fylp[k]));
+        for (int k = 0; k < N; ++k) qn[k] = update_2d(qp[k], sc, dxp[k], Fyu[k], Fylp[k]);
         store_row_volume<N>(dst + (int64_t)P * RS, qn, active, !periodic, x, P, hv_row + (P - 1) * 2 * N);
         Prim<2, C> t = primitives<2>(qn, g);
         const C l = max_eigenvalue<2>(t);
@@ -411,7 +428,7 @@ __device__ __forceinline__ void row2_interior(Row2<C> &st, const C (&q0)[4], Gas
     if (y > 0) {
         C qn[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) qn[k] = st.qp[k] - sc * (st.dxp[k] + (Fyl[k] - st.Fylp[k]));
+        for (int k = 0; k < N; ++k) qn[k] = update_2d(st.qp[k], sc, st.dxp[k], Fyl[k], st.Fylp[k]);
         store_row_volume<N>(dst + y * RS, qn, active, fixed, x, P, hv_row + (y - 1) * 2 * N);
         Prim<2, C> t = primitives<2>(qn, g);
         const C l = max_eigenvalue<2>(t);
@@ -451,7 +468,7 @@ __device__ __forceinline__ void row2_upper_halo(Row2<C> &st, const C (&q0)[4], G
     rusanov2<N>(st.qp, q0, st.Fyp, Fy, st.lyp, ly, Fyu);
     C qn[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) qn[k] = st.qp[k] - sc * (st.dxp[k] + (Fyu[k] - st.Fylp[k]));
+    for (int k = 0; k < N; ++k) qn[k] = update_2d(st.qp[k], sc, st.dxp[k], Fyu[k], st.Fylp[k]);
     store_row_volume<N>(dst + P * RS, qn, active, fixed, x, P, hv_row + (P - 1) * 2 * N);
     Prim<2, C> t = primitives<2>(qn, g);
     const C l = max_eigenvalue<2>(t);

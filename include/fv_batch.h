@@ -161,6 +161,17 @@ int fv_batch_set_cascade_layout(fv_batch_t *b, int layout);
  * arithmetic). */
 int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per_sm);
 
+/* Staging depth of the fused 2D sweep (Sec. 2.3 leaves the staging of the
+ * patch data to the realisation): the number of patch rows each warp keeps
+ * in flight in its shared-memory ring, for uniform 2D batches of edge 4, 8,
+ * 16 or 32 in FP32 or BF16 storage.  rows = 4 or 6, or 0 / 8 for the
+ * default depth of 8; the streaming launch shape (blocks_per_sm = -2) keeps
+ * its own ring.  Every depth computes the same bits; fv_batch_tune searches
+ * the depths together with the launch shapes and records its choice in the
+ * tuning cache.  FV_EINVAL for another value, FV_EUNSUPPORTED for a batch
+ * without the choice (depth unchanged). */
+int fv_batch_set_sweep_ring(fv_batch_t *b, int rows);
+
 /*
  * Register which patch lies across each face (the halo layer of width one
  * that the paper's framework fills from neighbouring patches before the

@@ -386,6 +386,7 @@ static int create_batch(fv_batch_t **out, int pde, int dim, int num_patches, con
     }
     b->plan.shape.warps_per_block = 4;
     b->plan.shape.blocks_per_sm = 0;
+    b->plan.shape.ring = 0;
 
     // Default form: fused sweep if the library has a kernel for the shapes, else the
     // patch-wise tile kernel, else the loop cascade.  Other PDEs than Euler
@@ -532,8 +533,21 @@ int fv_batch_set_launch_shape(fv_batch_t *b, int warps_per_block, int blocks_per
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     if (warps_per_block < 1 || warps_per_block > 16) return fail(FV_EINVAL, "warps_per_block must be in [1, 16]");
     if (blocks_per_sm < -2 || blocks_per_sm > 32) return fail(FV_EINVAL, "blocks_per_sm must be in [-2, 32]");
-    b->plan.shape = fv::FusedShape{warps_per_block, blocks_per_sm};
+    b->plan.shape = fv::FusedShape{warps_per_block, blocks_per_sm, b->plan.shape.ring};
     drop_graphs(b);
+    return FV_OK;
+}
+
+int fv_batch_set_sweep_ring(fv_batch_t *b, int rows)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (rows != 0 && rows != 4 && rows != 6 && rows != 8) return fail(FV_EINVAL, "ring depth must be 0, 4, 6 or 8");
+    if (rows == 8) rows = 0;                 // the default depth
+    if (rows != 0 && !(b->fused_kernel == fv::FUSED_SWEEP2D && fv::sweep_ring_applies(b->view, b->precision)))
+        return fail(FV_EUNSUPPORTED, "the ring depth is chosen for uniform 2D FP32/BF16 batches of edge 4, 8, 16 "
+                                     "or 32 only");
+    if (b->plan.shape.ring != rows) drop_graphs(b);
+    b->plan.shape.ring = rows;
     return FV_OK;
 }
 
@@ -810,9 +824,10 @@ int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len)
                      : (b->fused_kernel == fv::FUSED_SWEEP3D ? fv::fused3d_kernel_name(b->view, b->precision)
                                                              : "none");
     snprintf(buf, len, "form=%s precision=%s dim=%d patches=%d max_p=%d uniform_p=%d fused_kernel=%s "
-             "items=%d warps_per_block=%d blocks_per_sm=%d scratch_bytes=%zu cascade_layout=%s pde=%s",
+             "items=%d warps_per_block=%d blocks_per_sm=%d ring=%d scratch_bytes=%zu cascade_layout=%s pde=%s",
              form, prec, b->dim, b->T, b->view.max_p, b->view.uniform_p, fk, b->plan.num_items,
-             b->plan.shape.warps_per_block, b->plan.shape.blocks_per_sm, b->scratch_bytes, lay,
+             b->plan.shape.warps_per_block, b->plan.shape.blocks_per_sm,
+             b->plan.shape.ring ? b->plan.shape.ring : 8, b->scratch_bytes, lay,
              b->view.pde == fv::PDE_EULER ? "euler" : "shallow_water");
     return FV_OK;
 }
@@ -1073,9 +1088,14 @@ void load_tune_file()
     if (!path || !*path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char key[512];
-    int w, bps;
-    while (fscanf(f, "%511s %d %d", key, &w, &bps) == 3) g_tune_cache[key] = fv::FusedShape{w, bps};
+    // one line per batch signature: key, warps per block, blocks per SM and
+    // the ring depth (0 = default; absent in files written before it existed)
+    char line[640], key[512];
+    while (fgets(line, sizeof line, f)) {
+        int w = 0, bps = 0, ring = 0;
+        const int n = sscanf(line, "%511s %d %d %d", key, &w, &bps, &ring);
+        if (n >= 3) g_tune_cache[key] = fv::FusedShape{w, bps, n == 4 ? ring : 0};
+    }
     fclose(f);
 }
 
@@ -1086,7 +1106,9 @@ void save_tune_file()
     std::string tmp = std::string(path) + ".tmp";
     FILE *f = fopen(tmp.c_str(), "w");
     if (!f) return;
-    for (auto &kv : g_tune_cache) fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.warps_per_block, kv.second.blocks_per_sm);
+    for (auto &kv : g_tune_cache)
+        fprintf(f, "%s %d %d %d\n", kv.first.c_str(), kv.second.warps_per_block, kv.second.blocks_per_sm,
+                kv.second.ring);
     fclose(f);
     rename(tmp.c_str(), path);
 }
@@ -1116,7 +1138,7 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
     std::vector<unsigned char> ref(bytes), got(bytes);
     const int warps[] = {1, 2, 4, 8, 16};
     const int bps[] = {0, -1, -2, 1, 2, 4};
-    fv::FusedShape best{0, 0};
+    fv::FusedShape best{0, 0, 0};
     float best_ms = 1e30f;
     bool have_ref = false;
     cudaEvent_t e0, e1;
@@ -1149,12 +1171,22 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
         rc = fail(FV_ENOMEM, "autotune: eigenvalue/time-step scratch");
         goto done;
     }
-    for (int w : warps)
-        for (int k : bps) {
-            if (k > 0 && w * k > 64) continue;
-            if (w == 1 && k > 0) continue;
-            cands.push_back(fv::FusedShape{w, k});
-        }
+    {
+        // ring depths of the 2D sweep (rows in flight per warp): the default
+        // and, where the batch can choose, 4 and 6 -- instantiated kernels,
+        // timed and checked bitwise like the launch shapes
+        std::vector<int> rings{0};
+        if (b->fused_kernel == fv::FUSED_SWEEP2D && fv::sweep_ring_applies(b->view, b->precision))
+            rings.insert(rings.end(), {4, 6});
+        for (int r : rings)
+            for (int w : warps)
+                for (int k : bps) {
+                    if (k > 0 && w * k > 64) continue;
+                    if (w == 1 && k > 0) continue;
+                    if (r != 0 && k == -2) continue;     // the streaming schedule has its own ring
+                    cands.push_back(fv::FusedShape{w, k, r});
+                }
+    }
     {
         // every candidate once: results must be bitwise identical
         for (const fv::FusedShape &c : cands) {
@@ -1171,8 +1203,8 @@ extern "C" int fv_batch_tune(fv_batch_t *b, const void *Q_in, void *Q_out, const
                 ref = got;
                 have_ref = true;
             } else if (memcmp(ref.data(), got.data(), bytes) != 0) {
-                rc = fail(FV_ECUDA, "autotune: launch shape (%d warps, %d blocks/SM) changed the result",
-                          c.warps_per_block, c.blocks_per_sm);
+                rc = fail(FV_ECUDA, "autotune: launch shape (%d warps, %d blocks/SM, ring %d) changed the result",
+                          c.warps_per_block, c.blocks_per_sm, c.ring);
                 goto done;
             }
         }

@@ -59,7 +59,12 @@ void cascade_scratch_carve(void *base, const BatchView &b, int precision, Cascad
 struct FusedShape {
     int warps_per_block;       // 1..16
     int blocks_per_sm;         // grid = blocks_per_sm * SMs (persistent); 0 = one block per work item
+    int ring;                  // rows in flight per warp of the 2D sweep (FP32/BF16, one compiled edge):
+                               // 4 or 6; 0 = the default depth (8)
 };
+
+// true if the ring depth of the fused 2D sweep can be chosen for this batch
+bool sweep_ring_applies(const BatchView &b, int precision);
 
 // Work list of the fused sweep kernels: one item per group of equal-size
 // patches handled by one warp, largest patches first.

@@ -74,11 +74,11 @@ template <> struct RingDepth<double> { static constexpr int value = 4; };
 // Per-warp shared memory: 64 boundary faces and 64 x-halo volumes of N=4
 // values, 32 eigenvalue slots, and a ring of R rows of 32 volumes in
 // storage type.
-template <typename S>
+template <typename S, int R = RingDepth<S>::value>
 __host__ __device__ constexpr int warp_smem_bytes2d()
 {
     using C = typename StorageTraits<S>::Compute;
-    return (2 * 64 * 4 + 32) * (int)sizeof(C) + RingDepth<S>::value * 32 * 4 * (int)sizeof(S);
+    return (2 * 64 * 4 + 32) * (int)sizeof(C) + R * 32 * 4 * (int)sizeof(S);
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -495,14 +495,14 @@ __device__ __forceinline__ void boundary_face2(const C (&qL)[4], const C (&qR)[4
 // Compile-time edge P (32/P patches per warp): rows stream through a
 // per-warp shared-memory ring of R rows filled by cp.async, R-1 rows ahead
 // of the row being computed, so many loads are in flight without holding
-// registers.  Same arithmetic and order as sweep2d_item.
-template <typename S, typename C, int P>
+// registers.  Same arithmetic and order as sweep2d_item, whatever R.
+template <typename S, typename C, int P, int R = RingDepth<S>::value>
 __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem it, int lane,
                                             C *__restrict__ bface, C *__restrict__ hvol,
                                             C *__restrict__ red, unsigned char *__restrict__ ring,
                                             Health<C> &hl)
 {
-    constexpr int N = 4, E = P + 2, R = RingDepth<S>::value;
+    constexpr int N = 4, E = P + 2;
     constexpr int VB = 4 * (int)sizeof(S);
     constexpr int RS = E * N;
     const Gas<C> g = gas_of<C>(sp);
@@ -625,13 +625,13 @@ constexpr int sweep2d_min_blocks()
     return (P < 0 && sizeof(S) < 8) ? 2 : FV_SWEEP_MINB;
 }
 
-template <typename S, int P>
+template <typename S, int P, int R = RingDepth<S>::value>
 __global__ void __launch_bounds__(FV_SWEEP_MAXT, (sweep2d_min_blocks<S, P>())) k_sweep2d(SweepParams sp)
 {
     using C = typename StorageTraits<S>::Compute;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wbase = smem_raw + warp * warp_smem_bytes2d<S>();
+    unsigned char *wbase = smem_raw + warp * warp_smem_bytes2d<S, R>();
     C *bface = reinterpret_cast<C *>(wbase);
     C *hvol = bface + 64 * 4;
     C *red = hvol + 64 * 4;
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(FV_SWEEP_MAXT, (sweep2d_min_blocks<S, P>())) k
             it = sp.items[item];
         }
         if (P > 0) {
-            sweep2d_tpl<S, C, (P > 0 ? P : 4)>(sp, it, lane, bface, hvol, red, ring, hl);
+            sweep2d_tpl<S, C, (P > 0 ? P : 4), R>(sp, it, lane, bface, hvol, red, ring, hl);
         } else if (P < 0) {                 // every size class in one launch
             switch (it.p) {
             case 4: sweep2d_tpl<S, C, 4>(sp, it, lane, bface, hvol, red, ring, hl); break;
@@ -887,16 +887,16 @@ cudaError_t launch_stream(const SweepParams &sp, int wpb, cudaStream_t st)
 
 // Grid: one warp per item, or (persistent) blocks_per_sm blocks per SM,
 // where blocks_per_sm < 0 means as many as can be resident at once.
-template <typename S, int P>
+template <typename S, int P, int R = RingDepth<S>::value>
 cudaError_t launch_class(const SweepParams &sp, int wpb, int bps, cudaStream_t st)
 {
     static bool attr_set = false;
-    constexpr int kMaxWarpsSmem = kMaxBlockSmem / warp_smem_bytes2d<S>();
+    constexpr int kMaxWarpsSmem = kMaxBlockSmem / warp_smem_bytes2d<S, R>();
     wpb = std::min(wpb, kMaxWarpsSmem);
-    const int bytes = wpb * warp_smem_bytes2d<S>();
+    const int bytes = wpb * warp_smem_bytes2d<S, R>();
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep2d<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             std::min(kMaxWarpsPerBlock, kMaxWarpsSmem) * warp_smem_bytes2d<S>());
+        cudaError_t e = cudaFuncSetAttribute(k_sweep2d<S, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             std::min(kMaxWarpsPerBlock, kMaxWarpsSmem) * warp_smem_bytes2d<S, R>());
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -905,18 +905,30 @@ cudaError_t launch_class(const SweepParams &sp, int wpb, int bps, cudaStream_t s
         int per_sm = bps;
         if (per_sm < 0) {
             per_sm = 1;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep2d<S, P>, wpb * 32, bytes);
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep2d<S, P, R>, wpb * 32, bytes);
             if (e != cudaSuccess || per_sm < 1) per_sm = 1;
         }
         grid = std::min(grid, per_sm * num_sms());
     }
     if (grid < 1) grid = 1;
-    k_sweep2d<S, P><<<grid, wpb * 32, bytes, st>>>(sp);
+    k_sweep2d<S, P, R><<<grid, wpb * 32, bytes, st>>>(sp);
     return cudaGetLastError();
 }
 
+// compile-time edge p with a row ring of `ring` rows (4 or 6; otherwise the
+// default depth)
+template <typename S, int P>
+cudaError_t launch_class_ring(int ring, const SweepParams &sp, int wpb, int bps, cudaStream_t st)
+{
+    if (sizeof(S) < 8) {                    // FP32 / BF16 storage: ring depths are tuned
+        if (ring == 4) return launch_class<S, P, 4>(sp, wpb, bps, st);
+        if (ring == 6) return launch_class<S, P, 6>(sp, wpb, bps, st);
+    }
+    return launch_class<S, P>(sp, wpb, bps, st);
+}
+
 template <typename S>
-cudaError_t launch_class_p(int p, const SweepParams &sp, int wpb, int bps, cudaStream_t st)
+cudaError_t launch_class_p(int p, int ring, const SweepParams &sp, int wpb, int bps, cudaStream_t st)
 {
     if (bps == -2 && sp.uniform_elems && !sp.b.nbr) {   // streaming persistent warps (uniform batches)
         switch (p) {
@@ -928,10 +940,10 @@ cudaError_t launch_class_p(int p, const SweepParams &sp, int wpb, int bps, cudaS
         bps = -1;
     }
     switch (p) {
-    case 4: return launch_class<S, 4>(sp, wpb, bps, st);
-    case 8: return launch_class<S, 8>(sp, wpb, bps, st);
-    case 16: return launch_class<S, 16>(sp, wpb, bps, st);
-    case 32: return launch_class<S, 32>(sp, wpb, bps, st);
+    case 4: return launch_class_ring<S, 4>(ring, sp, wpb, bps, st);
+    case 8: return launch_class_ring<S, 8>(ring, sp, wpb, bps, st);
+    case 16: return launch_class_ring<S, 16>(ring, sp, wpb, bps, st);
+    case 32: return launch_class_ring<S, 32>(ring, sp, wpb, bps, st);
     default: return launch_class<S, 0>(sp, wpb, bps, st);
     }
 }
@@ -946,6 +958,12 @@ bool fused_reads_neighbours(const FusedPlan &plan)
         if (p != 4 && p != 8 && p != 16 && p != 32) return false;   // runtime-edge sweep reads own halos
     }
     return true;
+}
+
+bool sweep_ring_applies(const BatchView &b, int precision)
+{
+    const int p = b.uniform_p;
+    return b.dim == 2 && precision != PREC_F64 && (p == 4 || p == 8 || p == 16 || p == 32);
 }
 
 bool fused_supported(const BatchView &b, int precision, int *kernel)
@@ -1013,9 +1031,10 @@ cudaError_t launch_fused_update(const BatchView &b, int precision, const StepArg
         sp.counter = plan.work_counter + 2 * c;
         const int p = plan.class_p[c], bps = plan.shape.blocks_per_sm;
         cudaError_t e;
-        if (precision == PREC_F64) e = launch_class_p<double>(p, sp, wpb, bps, st);
-        else if (precision == PREC_F32) e = launch_class_p<float>(p, sp, wpb, bps, st);
-        else e = launch_class_p<__nv_bfloat16>(p, sp, wpb, bps, st);
+        const int ring = plan.shape.ring;
+        if (precision == PREC_F64) e = launch_class_p<double>(p, ring, sp, wpb, bps, st);
+        else if (precision == PREC_F32) e = launch_class_p<float>(p, ring, sp, wpb, bps, st);
+        else e = launch_class_p<__nv_bfloat16>(p, ring, sp, wpb, bps, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -48,6 +48,7 @@ _ERRNAMES = {FV_EINVAL: "FV_EINVAL", FV_ENOMEM: "FV_ENOMEM", FV_ECUDA: "FV_ECUDA
              FV_ETIMEOUT: "FV_ETIMEOUT"}
 
 EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_batch_set_launch_shape",
+           "fv_batch_set_sweep_ring",
            "fv_batch_set_neighbours", "fv_halo_exchange", "fv_patch_batch_update_host",
            "fv_patch_batch_update", "fv_max_eigenvalue", "fv_cfl_time_step",
            "fv_conserved_totals", "fv_batch_run", "fv_batch_tune", "fv_batch_status",
@@ -93,6 +94,7 @@ def load() -> ctypes.CDLL:
             "fv_batch_set_form": (i, [_vp, i]),
             "fv_batch_set_stream": (i, [_vp, _vp]),
             "fv_batch_set_launch_shape": (i, [_vp, i, i]),
+            "fv_batch_set_sweep_ring": (i, [_vp, i]),
             "fv_batch_test_wait_expiry": (i, [_vp, i]),
             "fv_batch_set_cascade_layout": (i, [_vp, i]),
             "fv_test_fail_device_alloc": (i, [i]),
@@ -177,6 +179,10 @@ def fv_halo_exchange(b, Q):
 
 def fv_batch_set_launch_shape(b, warps_per_block, blocks_per_sm):
     return _check(load().fv_batch_set_launch_shape(b, int(warps_per_block), int(blocks_per_sm)))
+
+
+def fv_batch_set_sweep_ring(b, rows):
+    return _check(load().fv_batch_set_sweep_ring(b, int(rows)))
 
 
 def fv_batch_create_pde(pde, dim, patch_size, precision, halo_mode, params, stream=0):
@@ -333,6 +339,9 @@ class FVBatch:
 
     def set_launch_shape(self, warps_per_block, blocks_per_sm):
         fv_batch_set_launch_shape(self.handle, warps_per_block, blocks_per_sm)
+
+    def set_sweep_ring(self, rows):
+        fv_batch_set_sweep_ring(self.handle, rows)
 
     def set_host_patches(self, patch_in, patch_out):
         """Register per-patch page-locked host buffers (see fv_batch_set_host_patches)."""

@@ -140,12 +140,28 @@ def test_workload5_full_size_sampled():
 
 # ------------------------------------------------------------ edge cases
 
+def _refuses_fused(w, precision):
+    """The fused form refuses a batch it has no kernel for, at creation, with
+    FV_EUNSUPPORTED (the caller then picks the tile or cascade form)."""
+    from paper_2306_16731_gb300 import fvbatch as fb
+    with pytest.raises(fb.FVError) as e:
+        fb.FVBatch(w.dim, w.patch_size, precision=precision, halo_mode=w.halo_mode, form=FORMS["fused"])
+    assert e.value.code == fb.FV_EUNSUPPORTED
+
+
 @pytest.mark.parametrize("form", ["cascade", "tile", "fused"])
 @pytest.mark.parametrize("dim,sizes", [(2, [1, 2, 3, 5, 7, 16, 17, 31, 32, 33, 4, 8]),
-                                       (3, [1, 2, 3, 4, 5, 8, 6, 7])])
+                                       (3, [1, 2, 3, 4, 5, 8, 6, 7, 16, 24, 10])])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_ragged_batches(form, dim, sizes, precision):
     w = inputs.uniform_batch(dim, sizes, seed=100 + dim, dx=np.linspace(0.05, 0.2, len(sizes)))
+    if form == "fused" and max(sizes) > (32 if dim == 2 else 16):
+        # fused 2D sweeps serve edges <= 32, fused 3D sweeps edges <= 16 (and
+        # uniform multiples of 8 up to 32): a batch with a larger patch is
+        # refused, the rest of it runs fused
+        _refuses_fused(w, precision)
+        keep = np.flatnonzero(w.patch_size <= (32 if dim == 2 else 16))
+        w = subset(w, keep)
     _check(w, precision, FORMS[form], 7)
 
 
@@ -165,9 +181,12 @@ def test_single_volume_patch():
 
 @pytest.mark.parametrize("dim,p", [(2, 1024), (3, 128)])
 def test_maximum_edge_length(dim, p):
+    """The largest edges the batch accepts run on the loop cascade; the
+    fused form has no kernel for them and says so."""
     w = inputs.uniform_batch(dim, [p], seed=9, dx=0.01)
     _check(w, 0, FORMS["cascade"], 1)
-    _check(w, 1, FORMS["fused"], 1)
+    _check(w, 1, FORMS["cascade"], 1)
+    _refuses_fused(w, 1)
 
 
 def test_empty_batch_is_a_no_op():
@@ -348,6 +367,81 @@ def test_launch_shapes_are_bitwise_identical(p, T, precision):
     # and the result is right
     ref, _, _ = oracle.batch_run(2, w.patch_size, w.dx, w.Q0.astype(np.float64), 5)
     assert batch_rel_linf(results[0][0], ref, 2, w.patch_size) < TOL[precision]
+
+
+@pytest.mark.parametrize("p,T,precision,halo", [(16, 700, 1, inputs.FIXED), (8, 333, 2, inputs.FIXED),
+                                                (32, 61, 1, inputs.PERIODIC), (4, 130, 1, inputs.FIXED),
+                                                (16, 5, 2, inputs.PERIODIC)])
+def test_sweep_ring_depths_are_bitwise_identical(p, T, precision, halo):
+    """Every staging depth of the 2D sweep (4, 6 or 8 rows in flight per
+    warp), with one-item-per-warp and persistent shapes, computes the same
+    bits over five CFL-chained steps, and the result is the oracle's."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(2, [p] * T, seed=80 + p, dx=np.linspace(0.01, 0.03, T), halo_mode=halo)
+    results = []
+    for ring, shape in [(0, (4, 0)), (4, (2, 0)), (6, (4, 0)), (4, (1, -1)), (6, (16, 1)), (8, (8, -1))]:
+        b = fb.FVBatch(2, w.patch_size, precision=precision, halo_mode=halo)
+        b.set_launch_shape(*shape)
+        b.set_sweep_ring(ring)
+        assert ("ring=%d" % (ring or 8)) in b.describe()
+        qa = to_device(w.Q0, precision)
+        qb = qa.clone()
+        dx = torch.tensor(w.dx, device="cuda")
+        lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+        dta, dtb = torch.zeros_like(lam), torch.zeros_like(lam)
+        b.max_eigenvalue(qa, lam)
+        b.cfl_time_step(lam, dx, 0.4, dta)
+        b.run(qa, qb, dx, dta, dtb, lam, 5, 0.4, use_graph=ring == 6)
+        b.status()
+        results.append((qb.to(torch.float64).cpu().numpy(), lam.cpu().numpy(), dtb.cpu().numpy()))
+        b.close()
+    for r in results[1:]:
+        for a_, b_ in zip(r, results[0]):
+            assert np.array_equal(a_, b_)
+    ref, lam_ref, _ = _oracle(w, precision, 5)
+    assert batch_rel_linf(results[0][0], ref, 2, w.patch_size) <= TOL[precision]
+    assert np.max(np.abs(results[0][1] - lam_ref) / lam_ref) <= TOL[precision]
+
+
+def test_sweep_ring_is_refused_where_it_has_no_choice():
+    from paper_2306_16731_gb300 import fvbatch as fb
+    for dim, sizes, prec in ((2, [16] * 4, 0), (2, [16, 8], 1), (2, [12] * 3, 1), (3, [8] * 2, 1)):
+        b = fb.FVBatch(dim, sizes, precision=prec)
+        with pytest.raises(fb.FVError) as e:
+            b.set_sweep_ring(4)
+        assert e.value.code == fb.FV_EUNSUPPORTED
+        assert "ring=8" in b.describe()
+        b.set_sweep_ring(0)                       # the default is always accepted
+        b.close()
+    b = fb.FVBatch(2, [16] * 4, precision=1)
+    with pytest.raises(fb.FVError) as e:
+        b.set_sweep_ring(5)
+    assert e.value.code == fb.FV_EINVAL
+    b.close()
+
+
+def test_tuner_records_shape_and_ring_depth(tmp_path, monkeypatch):
+    """fv_batch_tune times launch shapes and ring depths together (every
+    candidate checked bitwise against the first), keeps the fastest, and
+    writes it -- ring depth included -- to the tuning cache file."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("FVBATCH_TUNE_CACHE", str(cache))
+    w = inputs.uniform_batch(2, [16] * 777, seed=91, dx=0.02, dtype=np.float32)
+    b = fb.FVBatch(2, w.patch_size, precision=1)
+    qa = torch.from_numpy(w.Q0).cuda()
+    scratch = qa.clone()
+    dx = torch.tensor(w.dx, device="cuda")
+    dt = torch.full((777,), 1e-3, dtype=torch.float64, device="cuda")
+    b.tune(qa, scratch, dx, dt)
+    desc = b.describe()
+    line = [ln for ln in cache.read_text().splitlines() if "T777|" in ln and "prec1" in ln]
+    assert len(line) == 1
+    key, wpb, bps, ring = line[0].split()
+    assert ("warps_per_block=%s blocks_per_sm=%s ring=%d" % (wpb, bps, int(ring) or 8)) in desc
+    b.close()
 
 
 def test_tuner_picks_a_shape_and_keeps_results(tmp_path, monkeypatch):

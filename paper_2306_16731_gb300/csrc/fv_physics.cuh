@@ -254,15 +254,62 @@ __device__ __forceinline__ void rusanov2<4, float>(const float (&qL)[4], const f
     for (int k = 0; k < 4; ++k) Fh[k] = __fmaf_rn(nl, __fsub_rn(qR[k], qL[k]), __fadd_rn(FL[k], FR[k]));
 }
 
-// Update of one unknown from the doubled face fluxes:
-// Q_new = Q - (dt/2h) (dFx + (2Fy_up - 2Fy_low)), the x difference first.
+// 3D FP32, the same way: five unknowns (rho, rho u, rho v, rho w, E).
+template <>
+__device__ __forceinline__ Prim<3, float> primitives<3, float>(const float (&q)[5], Gas<float> g)
+{
+    Prim<3, float> s;
+    const float r = rcp_approx(q[0]);
+    s.u[0] = __fmul_rn(q[1], r);
+    s.u[1] = __fmul_rn(q[2], r);
+    s.u[2] = __fmul_rn(q[3], r);
+    const float kin = __fmaf_rn(q[3], s.u[2], __fmaf_rn(q[2], s.u[1], __fmul_rn(q[1], s.u[0])));
+    s.p = __fmul_rn(g.gm1, __fmaf_rn(-0.5f, kin, q[4]));
+    s.c = sqrt_approx(__fmul_rn(__fmul_rn(g.gamma, s.p), r));
+    return s;
+}
+
+template <>
+__device__ __forceinline__ float eigenvalue<3, float>(const Prim<3, float> &s, int n)
+{
+    return __fadd_rn(fabsf(s.u[n]), s.c);
+}
+
+template <>
+__device__ __forceinline__ float max_eigenvalue<3, float>(const Prim<3, float> &s)
+{
+    return __fadd_rn(fmaxf(fmaxf(fabsf(s.u[0]), fabsf(s.u[1])), fabsf(s.u[2])), s.c);
+}
+
+template <>
+__device__ __forceinline__ void flux<3, float>(const float (&q)[5], const Prim<3, float> &s, int n, float (&F)[5])
+{
+    const float un = s.u[n];
+    F[0] = q[1 + n];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[1 + a] = a == n ? __fmaf_rn(q[1 + a], un, s.p) : __fmul_rn(q[1 + a], un);
+    F[4] = __fmul_rn(__fadd_rn(q[4], s.p), un);
+}
+
+template <>
+__device__ __forceinline__ void rusanov2<5, float>(const float (&qL)[5], const float (&qR)[5], const float (&FL)[5],
+                                                   const float (&FR)[5], float lamL, float lamR, float (&Fh)[5])
+{
+    const float nl = -fmaxf(lamL, lamR);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Fh[k] = __fmaf_rn(nl, __fsub_rn(qR[k], qL[k]), __fadd_rn(FL[k], FR[k]));
+}
+
+// Update of one unknown from the doubled face fluxes: Q_new = Q - (dt/2h)
+// (d + (2F_up - 2F_low)), d the difference of the other directions (x, or
+// x then y), the last direction's difference formed first.
 template <typename C>
-__device__ __forceinline__ C update_2d(C q, C sc, C dfx, C fy_up, C fy_low)
+__device__ __forceinline__ C update_dq(C q, C sc, C dfx, C fy_up, C fy_low)
 {
     return q - sc * (dfx + (fy_up - fy_low));
 }
 template <>
-__device__ __forceinline__ float update_2d<float>(float q, float sc, float dfx, float fy_up, float fy_low)
+__device__ __forceinline__ float update_dq<float>(float q, float sc, float dfx, float fy_up, float fy_low)
 {
     return __fmaf_rn(-sc, __fadd_rn(dfx, __fsub_rn(fy_up, fy_low)), q);
 }

@@ -338,7 +338,7 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
         if (y > 0) {
             C qn[N];
 #pragma unroll
-            for (int k = 0; k < N; ++k) qn[k] = update_2d(qp[k], sc, dxp[k], Fyl[k], Fylp[k]);
+            for (int k = 0; k < N; ++k) qn[k] = update_dq(qp[k], sc, dxp[k], Fyl[k], Fylp[k]);
             store_row_volume<N>(dst + (int64_t)y * RS, qn, active, !periodic, x, P, hv_row + (y - 1) * 2 * N);   // row y-1 lives at y
             Prim<2, C> t = primitives<2>(qn, g);
             const C l = max_eigenvalue<2>(t);
@@ -378,7 +378,7 @@ __device__ __forceinline__ void sweep2d_item(const SweepParams sp, const WorkIte
         rusanov2<N>(qp, q0, Fyp, Fy, lyp, ly, Fyu);
         C qn[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) qn[k] = update_2d(qp[k], sc, dxp[k], Fyu[k], Fylp[k]);
+        for (int k = 0; k < N; ++k) qn[k] = update_dq(qp[k], sc, dxp[k], Fyu[k], Fylp[k]);
         store_row_volume<N>(dst + (int64_t)P * RS, qn, active, !periodic, x, P, hv_row + (P - 1) * 2 * N);
         Prim<2, C> t = primitives<2>(qn, g);
         const C l = max_eigenvalue<2>(t);
@@ -428,7 +428,7 @@ __device__ __forceinline__ void row2_interior(Row2<C> &st, const C (&q0)[4], Gas
     if (y > 0) {
         C qn[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) qn[k] = update_2d(st.qp[k], sc, st.dxp[k], Fyl[k], st.Fylp[k]);
+        for (int k = 0; k < N; ++k) qn[k] = update_dq(st.qp[k], sc, st.dxp[k], Fyl[k], st.Fylp[k]);
         store_row_volume<N>(dst + y * RS, qn, active, fixed, x, P, hv_row + (y - 1) * 2 * N);
         Prim<2, C> t = primitives<2>(qn, g);
         const C l = max_eigenvalue<2>(t);
@@ -468,7 +468,7 @@ __device__ __forceinline__ void row2_upper_halo(Row2<C> &st, const C (&q0)[4], G
     rusanov2<N>(st.qp, q0, st.Fyp, Fy, st.lyp, ly, Fyu);
     C qn[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) qn[k] = update_2d(st.qp[k], sc, st.dxp[k], Fyu[k], st.Fylp[k]);
+    for (int k = 0; k < N; ++k) qn[k] = update_dq(st.qp[k], sc, st.dxp[k], Fyu[k], st.Fylp[k]);
     store_row_volume<N>(dst + P * RS, qn, active, fixed, x, P, hv_row + (P - 1) * 2 * N);
     Prim<2, C> t = primitives<2>(qn, g);
     const C l = max_eigenvalue<2>(t);

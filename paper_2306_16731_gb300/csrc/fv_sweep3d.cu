@@ -120,7 +120,7 @@ __device__ __forceinline__ void finish3(int zz, const C (&upper)[5], const C (&q
     constexpr int N = 5;
     C qn[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) qn[k] = qp[k] - sc * (dxy[k] + (upper[k] - lower[k]));
+    for (int k = 0; k < N; ++k) qn[k] = update_dq(qp[k], sc, dxy[k], upper[k], lower[k]);
     const int64_t prow = (int64_t)(zz + 1) * EE + (y + 1) * E;
     store_volume<N>(qout + (prow + x + 1) * N, qn);
     Prim<3, C> st = primitives<3>(qn, g);
@@ -425,6 +425,32 @@ __device__ __forceinline__ void physics_sel(const C (&q)[5], Gas<C> g, bool ydir
     lam = fv_abs(un) + s.c;
 }
 
+// z planes per iteration of the 8x8-block kernel's plane loop
+#ifndef FV_B8_UNROLL
+#define FV_B8_UNROLL 2
+#endif
+constexpr int kB8Unroll = FV_B8_UNROLL;
+
+// Doubled Rusanov face between a ring volume r and the interior volume i
+// next to it: r is the lower-index side when ring_low, else the upper one.
+template <typename C>
+__device__ __forceinline__ void ring_face(const C (&qr)[5], const C (&qi)[5], const C (&Fr)[5], const C (&Fi)[5],
+                                          C lr, C li, bool ring_low, C (&Fh)[5])
+{
+    const C nl = ring_low ? -fv_max(lr, li) : fv_max(lr, li);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Fh[k] = (Fr[k] + Fi[k]) + nl * (qi[k] - qr[k]);
+}
+template <>
+__device__ __forceinline__ void ring_face<float>(const float (&qr)[5], const float (&qi)[5], const float (&Fr)[5],
+                                                 const float (&Fi)[5], float lr, float li, bool ring_low,
+                                                 float (&Fh)[5])
+{
+    const float nl = ring_low ? -fmaxf(lr, li) : fmaxf(lr, li);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Fh[k] = __fmaf_rn(nl, __fsub_rn(qi[k], qr[k]), __fadd_rn(Fr[k], Fi[k]));
+}
+
 template <typename S, typename C>
 __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plane_bytes, int chunk)
 {
@@ -486,6 +512,9 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
     }
     C lmax = C(0), min_rp = C(INFINITY), sum_l = C(0);
 
+    // planes two at a time: the carried values alternate between two
+    // register sets instead of being moved
+#pragma unroll (kB8Unroll)
     for (int z = -1; z <= P; ++z) {
         cp_wait<kRingB - 2>();
         __syncthreads();
@@ -536,15 +565,10 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
             const bool ydir = side >= 2, ring_low = (side & 1) == 0;
             physics_sel(qr, g, ydir, Fr, lr);
             physics_sel(qi, g, ydir, Fi, li);
-            C qL[N], qR[N], FL[N], FR[N];
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                qL[k] = ring_low ? qr[k] : qi[k];
-                qR[k] = ring_low ? qi[k] : qr[k];
-                FL[k] = ring_low ? Fr[k] : Fi[k];
-                FR[k] = ring_low ? Fi[k] : Fr[k];
-            }
-            rusanov2<N>(qL, qR, FL, FR, ring_low ? lr : li, ring_low ? li : lr, Fh);
+            // Eq. 2 with the lower volume first: for a ring volume above the
+            // interior one, swapping the sides only flips the sign of the
+            // dissipation term (exactly), so no operand needs selecting
+            ring_face(qr, qi, Fr, Fi, lr, li, ring_low, Fh);
 #pragma unroll
             for (int k = 0; k < N; ++k) bf[lane * N + k] = Fh[k];
         }

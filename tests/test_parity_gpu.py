@@ -140,12 +140,13 @@ def test_workload5_full_size_sampled():
 
 # ------------------------------------------------------------ edge cases
 
-def _refuses_fused(w, precision):
-    """The fused form refuses a batch it has no kernel for, at creation, with
-    FV_EUNSUPPORTED (the caller then picks the tile or cascade form)."""
+def _refuses_fused(w, precision, form="fused"):
+    """A form refuses a batch it has no kernel for, at creation, with
+    FV_EUNSUPPORTED (the caller then picks another form; the loop cascade
+    takes every batch)."""
     from paper_2306_16731_gb300 import fvbatch as fb
     with pytest.raises(fb.FVError) as e:
-        fb.FVBatch(w.dim, w.patch_size, precision=precision, halo_mode=w.halo_mode, form=FORMS["fused"])
+        fb.FVBatch(w.dim, w.patch_size, precision=precision, halo_mode=w.halo_mode, form=FORMS[form])
     assert e.value.code == fb.FV_EUNSUPPORTED
 
 
@@ -155,11 +156,12 @@ def _refuses_fused(w, precision):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_ragged_batches(form, dim, sizes, precision):
     w = inputs.uniform_batch(dim, sizes, seed=100 + dim, dx=np.linspace(0.05, 0.2, len(sizes)))
-    if form == "fused" and max(sizes) > (32 if dim == 2 else 16):
+    if form != "cascade" and max(sizes) > (32 if dim == 2 else 16):
         # fused 2D sweeps serve edges <= 32, fused 3D sweeps edges <= 16 (and
-        # uniform multiples of 8 up to 32): a batch with a larger patch is
-        # refused, the rest of it runs fused
-        _refuses_fused(w, precision)
+        # uniform multiples of 8 up to 32), the patch-wise kernel one thread
+        # per volume of a 2D patch (edge <= 32): a batch with a larger patch
+        # is refused, the rest of it runs in that form
+        _refuses_fused(w, precision, form)
         keep = np.flatnonzero(w.patch_size <= (32 if dim == 2 else 16))
         w = subset(w, keep)
     _check(w, precision, FORMS[form], 7)

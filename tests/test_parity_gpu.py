@@ -156,14 +156,15 @@ def _refuses_fused(w, precision, form="fused"):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_ragged_batches(form, dim, sizes, precision):
     w = inputs.uniform_batch(dim, sizes, seed=100 + dim, dx=np.linspace(0.05, 0.2, len(sizes)))
-    if form != "cascade" and max(sizes) > (32 if dim == 2 else 16):
+    if not _supported(w, precision, FORMS[form]):
         # fused 2D sweeps serve edges <= 32, fused 3D sweeps edges <= 16 (and
-        # uniform multiples of 8 up to 32), the patch-wise kernel one thread
-        # per volume of a 2D patch (edge <= 32): a batch with a larger patch
-        # is refused, the rest of it runs in that form
+        # uniform multiples of 8 up to 32), the patch-wise kernel patches
+        # that fit one block's shared memory: a batch with a larger patch is
+        # refused, and the rest of it runs in that form
         _refuses_fused(w, precision, form)
-        keep = np.flatnonzero(w.patch_size <= (32 if dim == 2 else 16))
-        w = subset(w, keep)
+        while not _supported(w, precision, FORMS[form]):
+            w = subset(w, np.flatnonzero(w.patch_size < w.patch_size.max()))
+        assert w.num_patches >= len(sizes) - 3
     _check(w, precision, FORMS[form], 7)
 
 

@@ -776,6 +776,11 @@ def other_workloads(dev, stream, flush_l2, steps):
         bpv = bytes_per_volume(ws, es)
         res[name] = {"value": ws.interior_volumes / (ms / 1e3), "ms_per_step": ms, "bytes_per_volume": bpv,
                      "roofline_frac": ws.interior_volumes * bpv / (ms / 1e3) / 1e9 / peak, "kernel": bs.describe()}
+        # the patch-wise form on the same batch, for comparison
+        bs.set_form(fb.FV_FORM_TILE)
+        mt = single_steps(bs, qs, dx, lam, dts, k, 0.4)
+        res[name]["patchwise_tile"] = {"value": ws.interior_volumes / (mt / 1e3), "ms_per_step": mt,
+                                       "roofline_frac": ws.interior_volumes * bpv / (mt / 1e3) / 1e9 / peak}
         bs.close()
         del qs
     # the 2D batch wired as a periodic 128 x 128 grid of patches: halos filled

@@ -126,8 +126,10 @@ int fv_batch_create(fv_batch_t **out, int dim, int num_patches,
  * Create a batch for one of the FV_PDE_* systems (Eq. 1; the paper studies
  * Euler only, Sec. 5).  params holds num_params values: Euler {gamma} (this
  * is fv_batch_create); shallow water {g > 0, f}, dim must be 2, precision
- * FV_F64 or FV_F32.  Other PDEs than Euler run on a generic patch-wise
- * kernel (FV_FORM_TILE, the only form set_form accepts for them): at each
+ * FV_F64 or FV_F32.  Other PDEs than Euler run on generic kernels that take
+ * the PDE as a device functor: a fused row sweep (FV_FORM_FUSED, the default
+ * when every edge is 4, 8, 16 or 32) or a patch-wise kernel (FV_FORM_TILE,
+ * the default otherwise); set_form accepts these two.  Both form at each
  * face the Rusanov flux of Eq. 2 on the evolved unknowns and the
  * non-conservative product B_n((Q_L+Q_R)/2)(Q_R - Q_L), half to each side;
  * Q_new = Q - dt/h sum_n [(Fhat_r - Fhat_l) + (D_r + D_l)/2] + dt S(Q);

@@ -314,8 +314,13 @@ static int create_batch(fv_batch_t **out, int pde, int dim, int num_patches, con
     probe.uniform_p = uni;
     probe.halo_mode = halo_mode;
     probe.align_bytes = align;
+    probe.pde = pde == FV_PDE_SHALLOW_WATER ? fv::PDE_SHALLOW_WATER : fv::PDE_EULER;
     if (pde == FV_PDE_EULER && num_patches > 0 && fv::fused_supported(probe, precision, &fk))
         build_work_list(b, order, b->items_h);
+    else if (pde != FV_PDE_EULER && fv::pde_fused_supported(probe, precision, patch_size)) {
+        fk = fv::FUSED_SWEEP_PDE;
+        build_work_list(b, order, b->items_h);
+    }
     b->fused_kernel = fk;
 
     // One device block: offsets, sizes, flags, work list, order, counter.
@@ -390,15 +395,19 @@ static int create_batch(fv_batch_t **out, int pde, int dim, int num_patches, con
 
     // Default form: fused sweep if the library has a kernel for the shapes, else the
     // patch-wise tile kernel, else the loop cascade.  Other PDEs than Euler
-    // run on the generic patch-wise kernel only.
+    // run on the generic fused sweep (edges 4, 8, 16, 32) or the generic
+    // patch-wise kernel.
     if (pde != FV_PDE_EULER) {
-        if (num_patches > 0 && !fv::pde_tile_supported(v, precision)) {
+        if (fk == fv::FUSED_SWEEP_PDE) {
+            b->form = FV_FORM_FUSED;
+        } else if (num_patches > 0 && !fv::pde_tile_supported(v, precision)) {
             cudaStreamDestroy(b->capture_stream);
             cudaFree(b->meta);
             delete b;
             return fail(FV_EUNSUPPORTED, "generic PDE kernel: patch too large for shared memory");
+        } else {
+            b->form = FV_FORM_TILE;
         }
-        b->form = FV_FORM_TILE;
     } else if (fk != fv::FUSED_NONE) b->form = FV_FORM_FUSED;
     else if (num_patches == 0 || fv::tile_supported(v, precision)) b->form = FV_FORM_TILE;
     else {
@@ -456,13 +465,15 @@ int fv_batch_set_form(fv_batch_t *b, int form)
     if (!b) return fail(FV_EINVAL, "batch is NULL");
     DeviceGuard dg(b->device);
     if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
-    if (b->view.pde != fv::PDE_EULER && form != FV_FORM_TILE)
-        return fail(FV_EUNSUPPORTED, "this PDE runs on the generic patch-wise kernel (FV_FORM_TILE) only");
+    if (b->view.pde != fv::PDE_EULER && form != FV_FORM_TILE && form != FV_FORM_FUSED)
+        return fail(FV_EUNSUPPORTED, "this PDE runs on the generic fused sweep or patch-wise kernel only");
+    if (b->view.pde != fv::PDE_EULER && form == FV_FORM_TILE && b->T > 0 && !fv::pde_tile_supported(b->view, b->precision))
+        return fail(FV_EUNSUPPORTED, "generic PDE kernel: patch too large for shared memory");
     if (form == FV_FORM_CASCADE || form == FV_FORM_TASKGRAPH) {
         int rc = ensure_scratch(b);
         if (rc) return rc;
     } else if (form == FV_FORM_TILE) {
-        if (b->T > 0 && !fv::tile_supported(b->view, b->precision))
+        if (b->view.pde == fv::PDE_EULER && b->T > 0 && !fv::tile_supported(b->view, b->precision))
             return fail(FV_EUNSUPPORTED, "patch-wise tile kernel: patch too large for shared memory");
     } else if (form == FV_FORM_FUSED) {
         if (b->T > 0 && b->fused_kernel == fv::FUSED_NONE)
@@ -620,7 +631,10 @@ static int launch_update(fv_batch_t *b, cudaStream_t st, const void *Q_in, void 
         e = b->view.pde == fv::PDE_EULER ? fv::launch_tile_update(b->view, b->precision, a, st)
                                          : fv::launch_pde_update(b->view, b->precision, a, st);
         break;
-    default: e = fv::launch_fused_update(b->view, b->precision, a, b->plan, st); break;
+    default:
+        e = b->plan.kernel == fv::FUSED_SWEEP_PDE ? fv::launch_pde_fused_update(b->view, b->precision, a, b->plan, st)
+                                                  : fv::launch_fused_update(b->view, b->precision, a, b->plan, st);
+        break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "update launch");
     return FV_OK;
@@ -820,7 +834,8 @@ int fv_batch_describe(const fv_batch_t *b, char *buf, size_t len)
                        : (b->form == FV_FORM_TILE ? "tile" : (b->form == FV_FORM_TASKGRAPH ? "taskgraph" : "fused"));
     const char *lay = b->cascade_layout == FV_LAYOUT_SOA ? "soa" : (b->cascade_layout == FV_LAYOUT_AOSOA ? "aosoa" : "aos");
     const char *prec = b->precision == FV_F64 ? "f64" : (b->precision == FV_F32 ? "f32" : "bf16/f32");
-    const char *fk = b->fused_kernel == fv::FUSED_SWEEP2D ? "sweep2d"
+    const char *fk = b->fused_kernel == fv::FUSED_SWEEP_PDE ? "sweep_pde"
+                     : b->fused_kernel == fv::FUSED_SWEEP2D ? "sweep2d"
                      : (b->fused_kernel == fv::FUSED_SWEEP3D ? fv::fused3d_kernel_name(b->view, b->precision)
                                                              : "none");
     snprintf(buf, len, "form=%s precision=%s dim=%d patches=%d max_p=%d uniform_p=%d fused_kernel=%s "
@@ -916,7 +931,8 @@ int enqueue_host_pipeline(fv_batch *b, cudaStream_t org, const HostPipeline &hp)
     const unsigned char *hi = static_cast<const unsigned char *>(hp.q_in);
     unsigned char *ho = static_cast<unsigned char *>(hp.q_out);
     const int C = hp.chunks;
-    const int per_item = hp.split ? (b->plan.kernel == fv::FUSED_SWEEP2D ? 32 / b->view.uniform_p : 1) : b->T;
+    const bool rows2d = b->plan.kernel == fv::FUSED_SWEEP2D || b->plan.kernel == fv::FUSED_SWEEP_PDE;
+    const int per_item = hp.split ? (rows2d ? 32 / b->view.uniform_p : 1) : b->T;
     const size_t arr = (size_t)b->T * sizeof(double);
     cudaEvent_t start = b->hs_events[2 * kMaxHostChunks], joined = b->hs_events[2 * kMaxHostChunks + 1];
     cudaError_t e = cudaEventRecord(start, org);      // order after earlier work on the stream
@@ -941,7 +957,8 @@ int enqueue_host_pipeline(fv_batch *b, cudaStream_t org, const HostPipeline &hp)
             sub.num_classes = 1;
             sub.class_begin[0] = item_lo;
             sub.class_end[0] = item_hi;
-            e = fv::launch_fused_update(b->view, b->precision, args, sub, org);
+            e = b->plan.kernel == fv::FUSED_SWEEP_PDE ? fv::launch_pde_fused_update(b->view, b->precision, args, sub, org)
+                                                      : fv::launch_fused_update(b->view, b->precision, args, sub, org);
             if (e != cudaSuccess) return cuda_fail(e, "host update launch");
         } else {
             const int rc = launch_update(b, org, qi, qo, d_dx, d_dt, args.lambda_out, args.dt_next_out, hp.cfl);

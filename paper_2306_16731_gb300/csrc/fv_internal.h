@@ -89,7 +89,7 @@ struct FusedPlan {
     int class_end[kMaxSizeClasses];
 };
 
-enum FusedKernel { FUSED_NONE = 0, FUSED_SWEEP2D = 1, FUSED_SWEEP3D = 2 };
+enum FusedKernel { FUSED_NONE = 0, FUSED_SWEEP2D = 1, FUSED_SWEEP3D = 2, FUSED_SWEEP_PDE = 3 };
 
 // Layout of the loop cascade's vector temporaries (F_n, face fluxes).
 enum CascadeLayout { CASCADE_AOS = 0, CASCADE_SOA = 1, CASCADE_AOSOA = 2 };
@@ -129,6 +129,11 @@ bool pde_tile_supported(const BatchView &b, int precision);
 cudaError_t launch_pde_update(const BatchView &b, int precision, const StepArgs &a, cudaStream_t st);
 cudaError_t launch_pde_max_eigenvalue(const BatchView &b, int precision, const void *q, double *lambda_out,
                                       cudaStream_t st);
+// Fused row sweep of a generic-PDE batch (fv_pde.cu): 2D, edges 4, 8, 16 or
+// 32 only (sizes_host: the T edge lengths), FP32 or FP64 storage.
+bool pde_fused_supported(const BatchView &b, int precision, const int32_t *sizes_host);
+cudaError_t launch_pde_fused_update(const BatchView &b, int precision, const StepArgs &a, const FusedPlan &plan,
+                                    cudaStream_t st);
 
 cudaError_t launch_halo_exchange(const BatchView &b, int precision, const int32_t *nbr, void *q,
                                  cudaStream_t st);

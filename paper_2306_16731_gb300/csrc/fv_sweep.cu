@@ -136,26 +136,6 @@ template <> __device__ __forceinline__ Gas<double> gas_of<double>(const SweepPar
 }
 
 // dt / (2h) in compute type (float arithmetic for float compute).
-// double -> float, rounded to nearest even, on the integer units: GB300's
-// FP64 unit, which also converts, is slow enough that a few conversions
-// per work item queue behind one another.  Normal float results only;
-// zero, subnormal, overflowing and non-finite inputs take the conversion
-// instruction.
-__device__ __forceinline__ float d2f_rn(double v)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned hi = (unsigned)(b >> 32);
-    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;      // float exponent field
-    if (e < 1 || e > 254) return float(v);
-    const unsigned long long m = b & 0xfffffffffffffull;            // 52 fraction bits
-    const unsigned long long rest = m & ((1ull << 29) - 1);          // the 29 bits rounded away
-    unsigned r = (unsigned)(m >> 29);
-    r += (rest > (1ull << 28) || (rest == (1ull << 28) && (r & 1u))) ? 1u : 0u;
-    // a carry out of the fraction moves into the exponent (and to infinity
-    // above the largest float), as rounding to nearest requires
-    return __uint_as_float((hi & 0x80000000u) | (((unsigned)e << 23) + r));
-}
-
 template <typename C> __device__ __forceinline__ C half_step_ratio(double dt, double h);
 template <> __device__ __forceinline__ float half_step_ratio<float>(double dt, double h)
 {

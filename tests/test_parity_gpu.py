@@ -879,10 +879,12 @@ def test_shallow_water_cfl_chained_run_and_graph_replay():
     assert batch_rel_linf(res[0][0], q, 2, w.patch_size) < 1e-12
 
 
-def test_shallow_water_lake_at_rest_keeps_zero_momentum_on_gpu():
+@pytest.mark.parametrize("form", ["fused", "tile"])
+def test_shallow_water_lake_at_rest_keeps_zero_momentum_on_gpu(form):
     import torch
     w = inputs.shallow_water_batch([16] * 8, seed=151, dx=0.1, depth_noise=0.0, speed=0.0, bottom=0.5)
-    b = _swe_batch(w, 0)
+    b = _swe_batch(w, 0, FORMS[form])
+    assert ("form=%s" % form) in b.describe()
     qa = to_device(w.Q0, 0)
     qb = qa.clone()
     dx = torch.tensor(w.dx, device="cuda")
@@ -906,12 +908,96 @@ def test_shallow_water_rejects_what_it_does_not_cover():
     with pytest.raises(fb.FVError) as e:
         fb.FVBatch(2, [4], pde=fb.FV_PDE_SHALLOW_WATER, params=[-1.0, 0.0])
     assert e.value.code == fb.FV_EINVAL
-    b = fb.FVBatch(2, [4, 8], pde=fb.FV_PDE_SHALLOW_WATER, params=[9.81, 0.0])
+    b = fb.FVBatch(2, [4, 12], pde=fb.FV_PDE_SHALLOW_WATER, params=[9.81, 0.0])
+    assert "form=tile" in b.describe()                    # edge 12: no fused sweep
     for form in (fb.FV_FORM_FUSED, fb.FV_FORM_CASCADE, fb.FV_FORM_TASKGRAPH):
         with pytest.raises(fb.FVError) as e:
             b.set_form(form)
         assert e.value.code == fb.FV_EUNSUPPORTED
     b.close()
+    b = fb.FVBatch(2, [4, 8], pde=fb.FV_PDE_SHALLOW_WATER, params=[9.81, 0.0])
+    assert "form=fused" in b.describe() and "fused_kernel=sweep_pde" in b.describe()
+    for form in (fb.FV_FORM_CASCADE, fb.FV_FORM_TASKGRAPH):
+        with pytest.raises(fb.FVError) as e:
+            b.set_form(form)
+        assert e.value.code == fb.FV_EUNSUPPORTED
+    b.set_form(fb.FV_FORM_TILE)
+    b.set_form(fb.FV_FORM_FUSED)
+    b.close()
+
+
+def _swe_one_step(b, w, precision, dt):
+    import torch
+    T = w.num_patches
+    qa = to_device(w.Q0, precision)
+    qb = qa.clone()
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dtn = torch.zeros_like(lam)
+    b.update(qa, qb, torch.tensor(w.dx, device="cuda"), torch.tensor(dt, device="cuda"), lam, dtn, 0.4)
+    b.status()
+    return qb.to(torch.float64).cpu().numpy(), lam.cpu().numpy(), dtn.cpu().numpy()
+
+
+@pytest.mark.parametrize("halo", [inputs.FIXED, inputs.PERIODIC])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("sizes", [[4, 8, 16, 32] * 5, [16] * 67])
+def test_shallow_water_fused_sweep_matches_oracle(halo, precision, sizes):
+    """The fused row sweep of the generic PDE (edges 4, 8, 16, 32): one step
+    against the oracle -- Rusanov flux, averaged non-conservative product,
+    Coriolis source -- with the eigenvalues and CFL steps of the new state and
+    the bathymetry copied bitwise; and within the same tolerance of the
+    patch-wise form on the same batch."""
+    w = inputs.shallow_water_batch(sizes, seed=171 + halo + len(sizes), dx=np.linspace(0.02, 0.1, len(sizes)),
+                                   halo_mode=halo)
+    b = _swe_batch(w, precision)
+    assert "form=fused" in b.describe() and "fused_kernel=sweep_pde" in b.describe()
+    q0 = initial_fp64(w.Q0, precision)
+    lam0 = oracle.swe_batch_max_eigenvalue(w.patch_size, q0, SWE_G)
+    dt = 0.4 * w.dx / (2 * lam0)
+    got, lam, dtn = _swe_one_step(b, w, precision, dt)
+    ref, lref = oracle.swe_batch_step(w.patch_size, w.dx, dt, q0, SWE_G, SWE_F, halo)
+    tol = 1e-12 if precision == 0 else 1e-5
+    assert batch_rel_linf(got, ref, 2, w.patch_size) < tol
+    assert np.max(np.abs(lam - lref) / lref) < tol
+    assert np.allclose(dtn, 0.4 * w.dx / (2 * lam), rtol=1e-15, atol=0)
+    for g_, q_ in zip(patches_interior(got, 2, w.patch_size), patches_interior(q0, 2, w.patch_size)):
+        assert np.array_equal(g_[..., 3], q_[..., 3])
+    b.set_form(FORMS["tile"])                             # the patch-wise form on the same batch
+    tile, _, _ = _swe_one_step(b, w, precision, dt)
+    assert batch_rel_linf(got, tile, 2, w.patch_size) < tol
+    b.close()
+
+
+def test_shallow_water_fused_sweep_chained_graph_and_launch_shapes():
+    """Ten CFL-chained fused steps: eager and as one CUDA graph bitwise equal,
+    every launch shape bitwise equal, and the oracle chained the same way
+    within FP64 tolerance."""
+    import torch
+    w = inputs.shallow_water_batch([16] * 40 + [8] * 21 + [32] * 5, seed=181, dx=0.05)
+    steps = 10
+    res = []
+    for shape, use_graph in (((4, 0), False), ((4, 0), True), ((2, -1), False), ((8, 1), True), ((1, 0), False)):
+        b = _swe_batch(w, 0)
+        b.set_launch_shape(*shape)
+        qa = to_device(w.Q0, 0)
+        qb = qa.clone()
+        dx = torch.tensor(w.dx, device="cuda")
+        lam = torch.zeros(w.num_patches, dtype=torch.float64, device="cuda")
+        dta, dtb = torch.zeros_like(lam), torch.zeros_like(lam)
+        b.max_eigenvalue(qa, lam)
+        b.cfl_time_step(lam, dx, 0.4, dta)
+        b.run(qa, qb, dx, dta, dtb, lam, steps, 0.4, use_graph)
+        b.status()
+        res.append(((qb if steps % 2 else qa).cpu().numpy(), lam.cpu().numpy()))
+        b.close()
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
+    q = w.Q0.astype(np.float64)
+    lamo = oracle.swe_batch_max_eigenvalue(w.patch_size, q, SWE_G)
+    for _ in range(steps):
+        dt = 0.4 * w.dx / (2 * lamo)
+        q, lamo = oracle.swe_batch_step(w.patch_size, w.dx, dt, q, SWE_G, SWE_F, w.halo_mode)
+    assert batch_rel_linf(res[0][0], q, 2, w.patch_size) < 1e-12
 
 
 # ------------------------------------------------- patches as separate host allocations

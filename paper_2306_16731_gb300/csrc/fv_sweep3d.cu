@@ -451,12 +451,13 @@ __device__ __forceinline__ void ring_face<float>(const float (&qr)[5], const flo
     for (int k = 0; k < 5; ++k) Fh[k] = __fmaf_rn(nl, __fsub_rn(qi[k], qr[k]), __fadd_rn(Fr[k], Fi[k]));
 }
 
-template <typename S, typename C>
+// PC > 0: the edge length compiled in (all index arithmetic folds); 0: sp.p.
+template <typename S, typename C, int PC>
 __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plane_bytes, int chunk)
 {
     constexpr int N = 5;
     extern __shared__ __align__(16) unsigned char smemb[];
-    const int P = sp.p, E = P + 2, EE = E * E, nb = P / 8;
+    const int P = PC > 0 ? PC : sp.p, E = P + 2, EE = E * E, nb = P / 8;
     const int ring_plane = (plane_bytes + 15) & ~15;
     unsigned char *ring = smemb;
     C *bfall = reinterpret_cast<C *>(ring + kRingB * ring_plane);
@@ -698,14 +699,17 @@ cudaError_t launch3b(const Sweep3Params &sp, int chunk, cudaStream_t st, int pre
     const int P = sp.p;
     const int plane_bytes = (P + 2) * (P + 2) * 5 * (int)sizeof(S);
     const size_t smem = smem3b_bytes(P, precision);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep3d_b8<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // the workloads' edges 8 and 16 compiled in, other multiples of 8 at run time
+    auto kern = P == 16 ? k_sweep3d_b8<S, C, 16> : (P == 8 ? k_sweep3d_b8<S, C, 8> : k_sweep3d_b8<S, C, 0>);
+    static bool attr[3] = {false, false, false};
+    const int ai = P == 16 ? 0 : (P == 8 ? 1 : 2);
+    if (!attr[ai]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[ai] = true;
     }
     const int threads = 32 * (P / 8) * (P / 8);
-    k_sweep3d_b8<S, C><<<sp.count, threads, smem, st>>>(sp, plane_bytes, std::min(chunk, pow2_align(plane_bytes)));
+    kern<<<sp.count, threads, smem, st>>>(sp, plane_bytes, std::min(chunk, pow2_align(plane_bytes)));
     return cudaGetLastError();
 }
 

@@ -346,10 +346,16 @@ __device__ __forceinline__ void pde_sweep_item(const PdeSweepParams &sp, const P
         if (active) {
             S *d = dst + (yf + 1) * RS;
             store_volume<N>(d, qn);
-            if (!periodic && (x == 0 || x == P - 1)) {     // whole rows: the x-halo volume keeps Q_in's value
+            // whole rows: the x-halo volumes keep Q_in's values
+            if (!periodic && x == 0) {
                 C hq[N];
-                load_volume<N>(hv + (yf * 2 + (x == 0 ? 0 : 1)) * N, hq);
-                store_volume<N>(d + (x == 0 ? -N : N), hq);
+                load_volume<N>(hv + (yf * 2) * N, hq);
+                store_volume<N>(d - N, hq);
+            }
+            if (!periodic && x == P - 1) {
+                C hq[N];
+                load_volume<N>(hv + (yf * 2 + 1) * N, hq);
+                store_volume<N>(d + N, hq);
             }
         }
         const C l = fv_max(ph.lambda(qn, 0), ph.lambda(qn, 1));

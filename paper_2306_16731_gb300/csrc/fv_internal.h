@@ -149,6 +149,10 @@ cudaError_t launch_conserved_totals(const BatchView &b, int precision, const voi
 
 int num_sms();
 
+// true if p is device memory (not mapped or managed host memory): the bulk
+// asynchronous copies of the 3D kernels address device memory only
+bool is_device_memory(const void *p);
+
 // Record the thread-local message returned by fv_last_error().
 void set_last_error(const char *msg);
 

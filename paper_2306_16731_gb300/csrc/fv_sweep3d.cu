@@ -21,6 +21,7 @@
 //     are written whole.
 #include <algorithm>
 
+#include "fv_bulk.cuh"
 #include "fv_common.cuh"
 
 namespace fv {
@@ -400,7 +401,24 @@ cudaError_t launch3(const Sweep3Params &sp, int chunk, cudaStream_t st, int prec
 //     neighbouring block's volumes) are computed first, one per lane, into
 //     shared memory, so no lane does extra face work inside the sweep;
 //   * z faces by the register recurrence, as in the general kernel.
+//   * Planes arrive in a ring of kRingB shared-memory slots, two planes
+//     ahead.  With BULK (device-resident state whose patches start on
+//     16-byte boundaries) thread 0 fetches each plane by one bulk
+//     asynchronous copy whose completion is counted on the slot's mbarrier,
+//     and every thread waits on that barrier, bounded in time: a wait that
+//     runs out ends the block at the next plane step, after thread 0 has
+//     waited (again bounded) for its copies in flight, and sets
+//     FV_FLAG_TIMEOUT.  Otherwise every thread copies its share of the
+//     plane in 16/8/4-byte cp.async chunks.
 constexpr int kRingB = 3;
+constexpr int kB8BarBytes = 32;      // the ring's mbarriers, at the start of shared memory
+
+// Bytes of one ring slot: a halo-inclusive plane, plus (bulk copies) up to
+// 15 bytes of 16-byte alignment padding on each side, rounded to 16 bytes.
+inline __host__ __device__ int b8_slot_bytes(int plane_bytes, bool bulk)
+{
+    return bulk ? (plane_bytes + 30 + 15) & ~15 : (plane_bytes + 15) & ~15;
+}
 
 template <int N, typename C>
 __device__ __forceinline__ void shfl_vec(C (&o)[N], const C (&v)[N], int delta, bool down)
@@ -452,14 +470,15 @@ __device__ __forceinline__ void ring_face<float>(const float (&qr)[5], const flo
 }
 
 // PC > 0: the edge length compiled in (all index arithmetic folds); 0: sp.p.
-template <typename S, typename C, int PC>
+template <typename S, typename C, int PC, bool BULK>
 __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plane_bytes, int chunk)
 {
     constexpr int N = 5;
     extern __shared__ __align__(16) unsigned char smemb[];
     const int P = PC > 0 ? PC : sp.p, E = P + 2, EE = E * E, nb = P / 8;
-    const int ring_plane = (plane_bytes + 15) & ~15;
-    unsigned char *ring = smemb;
+    const int ring_plane = b8_slot_bytes(plane_bytes, BULK);
+    unsigned char *ring = smemb + kB8BarBytes;
+    const unsigned bar0 = bulk::saddr(smemb);
     C *bfall = reinterpret_cast<C *>(ring + kRingB * ring_plane);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C *bf = bfall + warp * 32 * N;                   // this warp's 32 boundary faces
@@ -493,13 +512,51 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
 
     const unsigned ring_s = smem_addr(ring);
     auto src_plane = [&](int z) { return periodic ? wrap(z, P) : z; };
+    // bulk copies: plane z (memory plane src_plane(z) + 1) is fill (z+1)/kRingB
+    // of slot (z+1) % kRingB; the copied range is the plane widened to
+    // 16-byte boundaries (inside the patch, whose bytes are a multiple of
+    // 16), the plane starting at offset (start mod 16) of the slot
+    auto plane_src = [&](int z) { return gpatch + (int64_t)(src_plane(z) + 1) * plane_bytes; };
+    auto issue_bulk = [&](int z, unsigned extra) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(plane_src(z));
+        const uintptr_t lo = a & ~uintptr_t(15), hi = (a + (uintptr_t)plane_bytes + 15) & ~uintptr_t(15);
+        const int slot = (z + 1) % kRingB;
+        bulk::mbar_expect_tx(bar0 + 8u * slot, (unsigned)(hi - lo) + extra);
+        bulk::bulk_g2s(ring_s + slot * ring_plane, reinterpret_cast<const void *>(lo), (unsigned)(hi - lo),
+                       bar0 + 8u * slot);
+    };
+    auto bar_of = [&](int z) { return bar0 + 8u * (unsigned)((z + 1) % kRingB); };
+    auto parity_of = [&](int z) { return (unsigned)((z + 1) / kRingB) & 1u; };
+    bool timed_out = false;
+    int observed = -1, issued = -1;                  // thread 0: next plane not yet seen complete, last issued
+    // after a wait ran out: thread 0 lets the copies in flight land, then
+    // flags the batch; the caller returns
+    auto drain = [&]() {
+        if (threadIdx.x == 0) {
+            for (int t = observed; t <= issued; ++t) bulk::mbar_wait_bounded(bar_of(t), parity_of(t));
+            atomicOr(sp.b.flags, FV_FLAG_TIMEOUT);
+        }
+    };
+    if (BULK) {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < kRingB; ++i) bulk::mbar_init(bar0 + 8u * i, 1);
+            bulk::mbar_init_fence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int z = -1; z <= kRingB - 3 && z <= P; ++z) {
+                issue_bulk(z, z == -1 && sp.b.test_wait_expiry ? 16u : 0u);
+                issued = z;
+            }
+        }
+    } else {
 #pragma unroll
-    for (int rr = 0; rr < kRingB - 1; ++rr) {
-        const int z = rr - 1;
-        if (z <= P)
-            copy_plane(ring_s + ((z + 1) % kRingB) * ring_plane,
-                       gpatch + (int64_t)(src_plane(z) + 1) * plane_bytes, plane_bytes, chunk);
-        cp_commit();
+        for (int rr = 0; rr < kRingB - 1; ++rr) {
+            const int z = rr - 1;
+            if (z <= P)
+                copy_plane(ring_s + ((z + 1) % kRingB) * ring_plane, plane_src(z), plane_bytes, chunk);
+            cp_commit();
+        }
     }
 
     C qpA[N], FzpA[N], lzpA = C(0), dA[N], FlowA[N];
@@ -517,16 +574,28 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
     // register sets instead of being moved
 #pragma unroll (kB8Unroll)
     for (int z = -1; z <= P; ++z) {
-        cp_wait<kRingB - 2>();
-        __syncthreads();
-        {
-            const int zn = z + kRingB - 1;
-            if (zn <= P)
-                copy_plane(ring_s + ((zn + 1) % kRingB) * ring_plane,
-                           gpatch + (int64_t)(src_plane(zn) + 1) * plane_bytes, plane_bytes, chunk);
+        const int zn = z + kRingB - 1;
+        if (BULK) {
+            // every thread is done with plane z-1, whose slot plane zn takes
+            if (__syncthreads_or(timed_out)) {
+                drain();
+                return;
+            }
+            if (threadIdx.x == 0 && zn <= P) {
+                issue_bulk(zn, 0u);
+                issued = zn;
+            }
+            if (!bulk::mbar_wait_bounded(bar_of(z), parity_of(z))) timed_out = true;
+            else if (threadIdx.x == 0) observed = z + 1;
+        } else {
+            cp_wait<kRingB - 2>();
+            __syncthreads();
+            if (zn <= P) copy_plane(ring_s + ((zn + 1) % kRingB) * ring_plane, plane_src(zn), plane_bytes, chunk);
             cp_commit();
         }
-        const S *pl = reinterpret_cast<const S *>(ring + ((z + 1) % kRingB) * ring_plane);
+        const S *pl = reinterpret_cast<const S *>(
+            ring + ((z + 1) % kRingB) * ring_plane +
+            (BULK ? (int)(reinterpret_cast<uintptr_t>(plane_src(z)) & 15) : 0));
 
         if (z == -1 || z == P) {
             C qA[N], qB[N], FzA[N], FzB[N], lzA, lzB;
@@ -668,7 +737,14 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
         }
         __syncwarp();                                        // boundary faces consumed
     }
-    cp_wait<0>();
+    if (BULK) {
+        if (__syncthreads_or(timed_out)) {
+            drain();
+            return;
+        }
+    } else {
+        cp_wait<0>();
+    }
 
     const bool bad = !(min_rp > C(0)) || !(sum_l < C(INFINITY));
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(sp.b.flags, FV_FLAG_NONPHYSICAL);
@@ -682,25 +758,26 @@ __global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plan
     }
 }
 
-size_t smem3b_bytes(int P, int precision)
+size_t smem3b_bytes(int P, int precision, bool bulk)
 {
     const size_t E = P + 2, EE = E * E, N = 5;
     const size_t s = precision == PREC_F64 ? 8 : (precision == PREC_F32 ? 4 : 2);
     const size_t c = precision == PREC_F64 ? 8 : 4;
-    const size_t plane = (EE * N * s + 15) & ~size_t(15);
+    const size_t slot = (size_t)b8_slot_bytes((int)(EE * N * s), bulk);
     const size_t warps = (size_t)(P / 8) * (P / 8);
-    return kRingB * plane + warps * 32 * N * c + 32 * c;
+    return kB8BarBytes + kRingB * slot + warps * 32 * N * c + 32 * c;
 }
 
-template <typename S>
-cudaError_t launch3b(const Sweep3Params &sp, int chunk, cudaStream_t st, int precision)
+template <typename S, bool BULK>
+cudaError_t launch3b_t(const Sweep3Params &sp, int chunk, cudaStream_t st, int precision)
 {
     using C = typename StorageTraits<S>::Compute;
     const int P = sp.p;
     const int plane_bytes = (P + 2) * (P + 2) * 5 * (int)sizeof(S);
-    const size_t smem = smem3b_bytes(P, precision);
+    const size_t smem = smem3b_bytes(P, precision, BULK);
     // the workloads' edges 8 and 16 compiled in, other multiples of 8 at run time
-    auto kern = P == 16 ? k_sweep3d_b8<S, C, 16> : (P == 8 ? k_sweep3d_b8<S, C, 8> : k_sweep3d_b8<S, C, 0>);
+    auto kern = P == 16 ? k_sweep3d_b8<S, C, 16, BULK>
+                        : (P == 8 ? k_sweep3d_b8<S, C, 8, BULK> : k_sweep3d_b8<S, C, 0, BULK>);
     static bool attr[3] = {false, false, false};
     const int ai = P == 16 ? 0 : (P == 8 ? 1 : 2);
     if (!attr[ai]) {
@@ -711,6 +788,12 @@ cudaError_t launch3b(const Sweep3Params &sp, int chunk, cudaStream_t st, int pre
     const int threads = 32 * (P / 8) * (P / 8);
     kern<<<sp.count, threads, smem, st>>>(sp, plane_bytes, std::min(chunk, pow2_align(plane_bytes)));
     return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch3b(const Sweep3Params &sp, int chunk, cudaStream_t st, int precision, bool bulk)
+{
+    return bulk ? launch3b_t<S, true>(sp, chunk, st, precision) : launch3b_t<S, false>(sp, chunk, st, precision);
 }
 
 
@@ -775,10 +858,15 @@ cudaError_t launch_fused3d_update(const BatchView &b, int precision, const StepA
         // the block kernel needs 124 registers in float; double stays on the
         // general kernel (it would spill)
         const bool blocks8 = precision != PREC_F64 && sp.p % 8 == 0 && sp.p <= 32 &&
-                             smem3b_bytes(sp.p, precision) <= 227 * 1024;
+                             smem3b_bytes(sp.p, precision, true) <= 227 * 1024;
         if (blocks8) {
-            if (precision == PREC_F32) e = launch3b<float>(sp, chunk, st, precision);
-            else e = launch3b<__nv_bfloat16>(sp, chunk, st, precision);
+            // bulk plane copies: uniform batch (patch bases are multiples of
+            // the patch bytes), 16-byte aligned patches, device-resident input
+            const size_t E = sp.p + 2;
+            const bool bulk = b.uniform_p > 0 && (E * E * E * 5 * es) % 16 == 0 &&
+                              reinterpret_cast<uintptr_t>(a.q_in) % 16 == 0 && is_device_memory(a.q_in);
+            if (precision == PREC_F32) e = launch3b<float>(sp, chunk, st, precision, bulk);
+            else e = launch3b<__nv_bfloat16>(sp, chunk, st, precision, bulk);
         } else if (precision == PREC_F64) e = launch3<double>(sp, chunk, st, precision);
         else if (precision == PREC_F32) e = launch3<float>(sp, chunk, st, precision);
         else e = launch3<__nv_bfloat16>(sp, chunk, st, precision);

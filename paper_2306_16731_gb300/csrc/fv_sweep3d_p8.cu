@@ -31,6 +31,7 @@
 //     stride that touch ten sectors per warp instruction.
 #include <algorithm>
 
+#include "fv_bulk.cuh"
 #include "fv_common.cuh"
 #include "fv_pair.cuh"
 
@@ -39,6 +40,7 @@ namespace fv {
 namespace {
 
 using namespace pair;
+using namespace bulk;
 
 constexpr int kP = 8, kE = kP + 2;
 constexpr int kSlots = 5;                  // plane slots per warp
@@ -50,7 +52,6 @@ constexpr int kMaxWarps = 4;               // warps per block
 #define FV_P8_MIN_BLOCKS 4
 #endif
 constexpr int kStepsPerPatch = kP + 2;     // planes 7, 0..7, 0
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s per slot wait
 
 // 1: pair arithmetic as f32x2 instructions; 0: two scalar instructions per
 // pair (identical bits; kept for the packed-versus-scalar comparison)
@@ -73,86 +74,6 @@ struct P8Params {
     int count;                    // patches
     unsigned extra_tx;            // test hook: bytes the first plane wait expects beyond its copy
 };
-
-// ------------------------------------------------- mbarrier and bulk copies
-
-__device__ __forceinline__ unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_init_fence()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok)
-                 : "r"(bar), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase of `bar` with the given parity, at most kWaitLimitNs
-// (and at most 2^24 polls, should the global timer not advance).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
-{
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (unsigned polls = 0; !mbar_try(bar, parity); ++polls)
-        if (global_ns() - t0 > kWaitLimitNs || polls >= (1u << 24)) return false;
-    return true;
-}
-
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-// shared -> global bulk copy (async proxy), grouped per issuing thread
-__device__ __forceinline__ void bulk_s2g(void *dst, unsigned src, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(src), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-
-// every group has finished reading shared memory
-__device__ __forceinline__ void bulk_wait_read_0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-
-// all but the most recent group have finished reading shared memory
-__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory"); }
-
-// every group has completed
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-
-// generic-proxy shared-memory writes become visible to the async proxy
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
 
 // ------------------------------------------------------------------ kernel
 
@@ -463,12 +384,15 @@ bool fused3d_p8_applies(const BatchView &b, int precision, const void *q_in, con
         return false;
     // the bulk copies and stores address device memory only; mapped host
     // buffers (the direct host-state update) take the block kernel's loads
-    for (const void *ptr : {q_in, static_cast<const void *>(q_out)}) {
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
-            cudaGetLastError();
-            return false;
-        }
+    return is_device_memory(q_in) && is_device_memory(q_out);
+}
+
+bool is_device_memory(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return false;
     }
     return true;
 }

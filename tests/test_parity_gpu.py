@@ -691,18 +691,21 @@ def test_periodic_8cubed_warp_kernel_agrees_with_tile_form():
     assert batch_rel_linf(fused[0], tile[0], 3, w.patch_size) < 1e-5
 
 
-def test_bounded_copy_wait_reports_timeout_and_context_survives():
+@pytest.mark.parametrize("p,halo,kernel", [(8, inputs.PERIODIC, "sweep3d_p8"), (16, inputs.FIXED, "sweep3d_b8")])
+def test_bounded_copy_wait_reports_timeout_and_context_survives(p, halo, kernel):
     """A plane wait that can never complete (the test hook makes it expect 16
     bytes more than its copy delivers) gives up after its 1 s bound: the
     update reports FV_ETIMEOUT, nothing faults, and the next normal update
-    on the same context matches the oracle."""
+    on the same context matches the oracle.  Both kernels that fetch planes
+    by bulk copies: the one-warp periodic 8^3 kernel and the 8x8-block
+    kernel (16^3, fixed halos)."""
     import time
     import torch
     from paper_2306_16731_gb300 import fvbatch as fb
     T = 6
-    w = inputs.uniform_batch(3, [8] * T, seed=99, halo_mode=inputs.PERIODIC, dtype=np.float32)
-    b = fb.FVBatch(3, w.patch_size, precision=1, halo_mode=inputs.PERIODIC)
-    assert "sweep3d_p8" in b.describe()
+    w = inputs.uniform_batch(3, [p] * T, seed=99, halo_mode=halo, dtype=np.float32)
+    b = fb.FVBatch(3, w.patch_size, precision=1, halo_mode=halo)
+    assert kernel in b.describe()
     qa = to_device(w.Q0, 1)
     qb = torch.zeros_like(qa)
     dx = torch.tensor(w.dx, device="cuda")
@@ -719,8 +722,7 @@ def test_bounded_copy_wait_reports_timeout_and_context_survives():
     b.test_wait_expiry(False)
     b.update(qa, qb, dx, dt, lam, None, 0.4)
     b.status()
-    ref, lam_ref = oracle.batch_step(3, w.patch_size, w.dx, [1e-3] * T, initial_fp64(w.Q0, 1),
-                                     halo_mode=inputs.PERIODIC)
+    ref, lam_ref = oracle.batch_step(3, w.patch_size, w.dx, [1e-3] * T, initial_fp64(w.Q0, 1), halo_mode=halo)
     assert batch_rel_linf(qb.to(torch.float64).cpu().numpy(), ref, 3, w.patch_size) < 1e-5
     b.close()
 

@@ -483,6 +483,45 @@ def test_3d_block_kernel_periodic_conservation_and_graph(p, T):
     b.close()
 
 
+@pytest.mark.parametrize("p,halo,T", [(8, inputs.FIXED, 40), (16, inputs.FIXED, 9), (16, inputs.PERIODIC, 7),
+                                      (24, inputs.FIXED, 5), (32, inputs.PERIODIC, 3)])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_3d_block_kernel_bulk_plane_copies(p, halo, T, precision):
+    """The 8x8-block 3D kernel fetches each plane of a device-resident uniform
+    batch by one bulk copy (BF16 planes, whose bytes are not multiples of
+    16, through the range widened to 16-byte boundaries), and the planes of
+    mapped host buffers by per-thread chunk copies.  Both give the same bits,
+    for compiled (8, 16) and run-time (24, 32) edges, and match the oracle."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(3, [p] * T, seed=140 + p, dx=np.linspace(0.02, 0.04, T), halo_mode=halo)
+    b = fb.FVBatch(3, w.patch_size, precision=precision, halo_mode=halo)
+    if p != 8 or halo != inputs.PERIODIC:
+        assert "sweep3d_b8" in b.describe()
+    qa = to_device(w.Q0, precision)
+    qb = torch.zeros_like(qa)
+    dx = torch.tensor(w.dx, device="cuda")
+    dt = torch.full((T,), 1e-3, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dtn = torch.zeros_like(lam)
+    b.update(qa, qb, dx, dt, lam, dtn, 0.4)
+    torch.cuda.synchronize()
+    hin = qa.cpu().pin_memory()
+    hout = torch.zeros_like(hin).pin_memory()
+    hl = torch.zeros(T, dtype=torch.float64).pin_memory()
+    hd = torch.zeros(T, dtype=torch.float64).pin_memory()
+    b.update_host(hin, hout, dx.cpu().pin_memory(), dt.cpu().pin_memory(), hl, hd, 0.4, 0)   # mapped buffers
+    got = patches_interior(qb.to(torch.float64).cpu().numpy(), 3, w.patch_size)
+    mapped = patches_interior(hout.to(torch.float64).numpy(), 3, w.patch_size)
+    assert all(np.array_equal(g, m) for g, m in zip(got, mapped))
+    assert np.array_equal(hl.numpy(), lam.cpu().numpy()) and np.array_equal(hd.numpy(), dtn.cpu().numpy())
+    ref, lam_ref = oracle.batch_step(3, w.patch_size, w.dx, [1e-3] * T, initial_fp64(w.Q0, precision), halo_mode=halo)
+    tol = TOL[precision] if precision == 1 else 1e-2
+    assert batch_rel_linf(qb.to(torch.float64).cpu().numpy(), ref, 3, w.patch_size) <= tol
+    assert np.max(np.abs(lam.cpu().numpy() - lam_ref) / lam_ref) <= tol
+    b.close()
+
+
 @pytest.mark.parametrize("dim,p", [(2, 16), (2, 8), (3, 8)])
 def test_bfloat16_storage_error_is_stated_and_bounded(dim, p):
     w = inputs.uniform_batch(dim, [p] * 64, seed=70 + p, dx=0.02)

@@ -316,8 +316,10 @@ int fv_batch_run(fv_batch_t *b, void *Q_a, void *Q_b, const double *dx,
 
 /*
  * Autotune the fused form: time every candidate launch shape of this
- * batch's kernel on the given buffers (contents of Q_out are overwritten),
- * check that every candidate's output is bitwise identical to the first
+ * batch's kernel on the given buffers.  Q_out is scratch: it is zeroed
+ * before each candidate, so afterwards its contents, halo volumes included,
+ * are unspecified (pass a buffer other than the next step's input).  The
+ * tuner checks that every candidate's output is bitwise identical to the first
  * one's, and keep the fastest.  Each timed launch follows a read of a
  * scratch buffer twice the size of L2 (allocated for the call, FV_ENOMEM if
  * it cannot be), so candidates are timed with their input in HBM.  Results are cached per device and batch

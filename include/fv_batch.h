@@ -277,13 +277,45 @@ int fv_patch_batch_update(fv_batch_t *b, const void *Q_in, void *Q_out,
  * same buffers; a cached graph is dropped when a buffer is no longer
  * page-locked, and by the calls that drop the update graphs (form, launch
  * shape, tuning, neighbour table).
- * Synchronous: returns when Q_out_host and the outputs are complete.  The
- * halo volumes of Q_out_host are unspecified.
+ * Synchronous: returns when Q_out_host and the outputs are complete.  With
+ * chunks >= 1 and fixed halos the halo volumes of Q_out_host are those of
+ * Q_in_host (so steps chain); with periodic halos they are unspecified;
+ * with chunks = 0 they are as after fv_patch_batch_update.
  */
 int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, void *Q_out_host,
                                const double *dx_host, const double *dt_host,
                                double *lambda_host, double *dt_next_host, double cfl,
                                int chunks);
+
+/*
+ * `steps` CFL-chained updates of a batch whose state lives in HOST memory,
+ * every step's state copied to the device and back (the host-resident
+ * patches of Sec. 4 "Data transfer" and Sec. 5, over a time-stepping loop).
+ * Q_a_host / Q_b_host: host state buffers (page-locked for full speed);
+ * step s reads Q_a (s even) or Q_b (s odd) and writes the other, so the
+ * final state is in Q_b if steps is odd, else in Q_a.  dx_host: num_patches
+ * doubles, copied once.  dt_a_host holds the first step's time steps; step
+ * s reads dt_a (s even) or dt_b (s odd) and writes the CFL time steps of
+ * its new state, dt = cfl dx / (d lambda), into the other (both num_patches
+ * doubles, host).  lambda_host (may be NULL): the eigenvalues of the final
+ * state.  chunks in 1..64 as in fv_patch_batch_update_host: for a uniform
+ * batch in the fused form the patches are cut into that many ranges, and
+ * each range runs as a chain through the steps -- its state and time steps
+ * in, its update, its state and next time steps out, then its next step's
+ * copy in -- while the chains of the other ranges proceed independently, so
+ * one step's copies out overlap the next step's copies in; any other batch
+ * runs as one range.  Results are bitwise those of `steps` calls of
+ * fv_patch_batch_update_host with the buffers alternated.  steps = 0 or an
+ * empty batch: no-op.  FV_EINVAL for NULL pointers, steps < 0, chunks
+ * outside 1..64, a non-positive cfl, or overlapping Q_a/Q_b or dt_a/dt_b;
+ * the device staging is that of fv_patch_batch_update_host (FV_ENOMEM).
+ * Synchronous: returns when the final state and outputs are on the host.
+ * With fixed halos every state written keeps the first state's halo
+ * volumes; with periodic halos the halo volumes written are unspecified.
+ */
+int fv_patch_batch_run_host(fv_batch_t *b, void *Q_a_host, void *Q_b_host, const double *dx_host,
+                            double *dt_a_host, double *dt_b_host, double *lambda_host, int steps,
+                            double cfl, int chunks);
 
 /* Per-patch maximum eigenvalue of Q (Sec. 2.2, Sec. 4 "Reduction"):
  * lambda_out[i] = max over interior volumes and directions n of |u_n| + c

@@ -866,7 +866,7 @@ int host_staging(fv_batch *b)
     if (e == cudaSuccess) e = dev_alloc(&arr, 4 * (size_t)b->T * sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ci, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking);
-    for (int i = 0; e == cudaSuccess && i < 2 * kMaxHostChunks + 2; ++i) {
+    for (int i = 0; e == cudaSuccess && i < 3 * kMaxHostChunks + 2; ++i) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) evs.push_back(ev);
@@ -918,6 +918,44 @@ bool all_page_locked(const HostPipeline &hp)
            page_locked(hp.lambda) && page_locked(hp.dt_next);
 }
 
+// Patches [p_lo, p_hi) and work items [item_lo, item_hi) of chunk c of C
+// (split: ranges of the uniform fused batch's work list; otherwise chunk 0
+// is the whole batch).
+struct ChunkRange {
+    int item_lo, item_hi, p_lo, p_hi;
+    size_t byte_off, bytes;
+};
+
+ChunkRange chunk_range(const fv_batch *b, bool split, int c, int C)
+{
+    const bool rows2d = b->plan.kernel == fv::FUSED_SWEEP2D || b->plan.kernel == fv::FUSED_SWEEP_PDE;
+    const int per_item = split ? (rows2d ? 32 / b->view.uniform_p : 1) : b->T;
+    ChunkRange r;
+    r.item_lo = split ? (int)((int64_t)b->plan.num_items * c / C) : 0;
+    r.item_hi = split ? (int)((int64_t)b->plan.num_items * (c + 1) / C) : 0;
+    r.p_lo = split ? std::min(b->T, r.item_lo * per_item) : 0;
+    r.p_hi = split ? std::min(b->T, r.item_hi * per_item) : b->T;
+    const size_t es = elem_bytes(b->precision);
+    r.byte_off = (size_t)b->elem_off[r.p_lo] * es;
+    r.bytes = (size_t)(b->elem_off[r.p_hi] - b->elem_off[r.p_lo]) * es;
+    return r;
+}
+
+// The update of one chunk's patches on stream st (the whole batch when not
+// split).
+int launch_chunk(fv_batch *b, cudaStream_t st, bool split, const ChunkRange &r, const fv::StepArgs &a)
+{
+    if (!split) return launch_update(b, st, a.q_in, a.q_out, a.dx, a.dt, a.lambda_out, a.dt_next_out, a.cfl);
+    fv::FusedPlan sub = b->plan;
+    sub.num_classes = 1;
+    sub.class_begin[0] = r.item_lo;
+    sub.class_end[0] = r.item_hi;
+    const cudaError_t e = b->plan.kernel == fv::FUSED_SWEEP_PDE
+                              ? fv::launch_pde_fused_update(b->view, b->precision, a, sub, st)
+                              : fv::launch_fused_update(b->view, b->precision, a, sub, st);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "host update launch");
+}
+
 // Enqueue one host-state update on stream `org`: dx and dt of every patch in
 // once, then per chunk its state in (copy-in stream), its update (org) and
 // its state out (copy-out stream), so the copies of neighbouring chunks
@@ -925,14 +963,11 @@ bool all_page_locked(const HostPipeline &hp)
 // after the last update; the copy streams join `org` at the end.
 int enqueue_host_pipeline(fv_batch *b, cudaStream_t org, const HostPipeline &hp)
 {
-    const size_t es = elem_bytes(b->precision);
     double *d_dx = b->hs_arrays, *d_dt = d_dx + b->T, *d_lam = d_dt + b->T, *d_dtn = d_lam + b->T;
     unsigned char *qi = static_cast<unsigned char *>(b->hs_in), *qo = static_cast<unsigned char *>(b->hs_out);
     const unsigned char *hi = static_cast<const unsigned char *>(hp.q_in);
     unsigned char *ho = static_cast<unsigned char *>(hp.q_out);
     const int C = hp.chunks;
-    const bool rows2d = b->plan.kernel == fv::FUSED_SWEEP2D || b->plan.kernel == fv::FUSED_SWEEP_PDE;
-    const int per_item = hp.split ? (rows2d ? 32 / b->view.uniform_p : 1) : b->T;
     const size_t arr = (size_t)b->T * sizeof(double);
     cudaEvent_t start = b->hs_events[2 * kMaxHostChunks], joined = b->hs_events[2 * kMaxHostChunks + 1];
     cudaError_t e = cudaEventRecord(start, org);      // order after earlier work on the stream
@@ -941,29 +976,20 @@ int enqueue_host_pipeline(fv_batch *b, cudaStream_t org, const HostPipeline &hp)
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_dx, hp.dx, arr, cudaMemcpyHostToDevice, b->hs_copy_in);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_dt, hp.dt, arr, cudaMemcpyHostToDevice, b->hs_copy_in);
     for (int c = 0; c < C && e == cudaSuccess; ++c) {
-        const int item_lo = hp.split ? (int)((int64_t)b->plan.num_items * c / C) : 0;
-        const int item_hi = hp.split ? (int)((int64_t)b->plan.num_items * (c + 1) / C) : 0;
-        const int p_lo = hp.split ? std::min(b->T, item_lo * per_item) : 0;
-        const int p_hi = hp.split ? std::min(b->T, item_hi * per_item) : b->T;
-        const size_t o = (size_t)b->elem_off[p_lo] * es, n = (size_t)(b->elem_off[p_hi] - b->elem_off[p_lo]) * es;
+        const ChunkRange r = chunk_range(b, hp.split, c, C);
+        const size_t o = r.byte_off, n = r.bytes;
         cudaEvent_t ev_in = b->hs_events[2 * c], ev_done = b->hs_events[2 * c + 1];
         e = cudaMemcpyAsync(qi + o, hi + o, n, cudaMemcpyHostToDevice, b->hs_copy_in);
         if (e == cudaSuccess) e = cudaEventRecord(ev_in, b->hs_copy_in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(org, ev_in, 0);
         if (e != cudaSuccess) break;
+        // fixed halos: the staged output starts as the input, so the halo
+        // volumes the update leaves untouched go back as Q_in's
+        if (b->halo_mode == FV_HALO_FIXED) e = cudaMemcpyAsync(qo + o, qi + o, n, cudaMemcpyDeviceToDevice, org);
+        if (e != cudaSuccess) break;
         fv::StepArgs args{qi, qo, d_dx, d_dt, hp.lambda ? d_lam : nullptr, hp.dt_next ? d_dtn : nullptr, hp.cfl};
-        if (hp.split) {
-            fv::FusedPlan sub = b->plan;
-            sub.num_classes = 1;
-            sub.class_begin[0] = item_lo;
-            sub.class_end[0] = item_hi;
-            e = b->plan.kernel == fv::FUSED_SWEEP_PDE ? fv::launch_pde_fused_update(b->view, b->precision, args, sub, org)
-                                                      : fv::launch_fused_update(b->view, b->precision, args, sub, org);
-            if (e != cudaSuccess) return cuda_fail(e, "host update launch");
-        } else {
-            const int rc = launch_update(b, org, qi, qo, d_dx, d_dt, args.lambda_out, args.dt_next_out, hp.cfl);
-            if (rc) return rc;
-        }
+        const int rc = launch_chunk(b, org, hp.split, r, args);
+        if (rc) return rc;
         e = cudaEventRecord(ev_done, org);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->hs_copy_out, ev_done, 0);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ho + o, qo + o, n, cudaMemcpyDeviceToHost, b->hs_copy_out);
@@ -1061,6 +1087,100 @@ extern "C" int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, 
     if (rc) return rc;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? FV_OK : cuda_fail(e, "host update");
+}
+
+// ------------------------------------------- host-resident time stepping
+
+extern "C" int fv_patch_batch_run_host(fv_batch_t *b, void *Q_a_host, void *Q_b_host, const double *dx_host,
+                                       double *dt_a_host, double *dt_b_host, double *lambda_host, int steps,
+                                       double cfl, int chunks)
+{
+    if (!b) return fail(FV_EINVAL, "batch is NULL");
+    if (steps < 0) return fail(FV_EINVAL, "steps must be >= 0");
+    if (chunks < 1 || chunks > kMaxHostChunks) return fail(FV_EINVAL, "chunks must be in [1, %d]", kMaxHostChunks);
+    if (!(cfl > 0.0 && cfl < 1e300)) return fail(FV_EINVAL, "cfl must be finite and > 0");
+    if (b->T == 0 || steps == 0) return FV_OK;
+    if (!Q_a_host || !Q_b_host || !dx_host || !dt_a_host || !dt_b_host) return fail(FV_EINVAL, "NULL host pointer");
+    const size_t bytes = (size_t)b->state_elems * elem_bytes(b->precision);
+    const size_t arr = (size_t)b->T * sizeof(double);
+    if (overlaps(Q_a_host, Q_b_host, bytes)) return fail(FV_EINVAL, "Q_a and Q_b overlap");
+    if (overlaps(dt_a_host, dt_b_host, arr)) return fail(FV_EINVAL, "dt_a and dt_b overlap");
+    DeviceGuard dg(b->device);
+    if (!dg.ok) return fail(FV_ECUDA, "cannot make device %d current", b->device);
+    int rc = host_staging(b);
+    if (rc) return rc;
+
+    const bool split = b->form == FV_FORM_FUSED && b->view.uniform_p > 0 && b->plan.num_classes == 1 &&
+                       !b->view.nbr && chunks > 1;
+    const int C = split ? std::min(chunks, b->plan.num_items) : 1;
+    double *d_dx = b->hs_arrays, *d_dt = d_dx + b->T, *d_lam = d_dt + b->T, *d_dtn = d_lam + b->T;
+    unsigned char *qi = static_cast<unsigned char *>(b->hs_in), *qo = static_cast<unsigned char *>(b->hs_out);
+    unsigned char *hq[2] = {static_cast<unsigned char *>(Q_a_host), static_cast<unsigned char *>(Q_b_host)};
+    double *hdt[2] = {dt_a_host, dt_b_host};
+    cudaStream_t org = b->stream, cin = b->hs_copy_in, cout = b->hs_copy_out;
+    cudaEvent_t start = b->hs_events[2 * kMaxHostChunks], joined = b->hs_events[2 * kMaxHostChunks + 1];
+    std::vector<ChunkRange> ranges;
+    for (int c = 0; c < C; ++c) ranges.push_back(chunk_range(b, split, c, C));
+
+    // Per chunk a chain through the steps: copy in (state and time steps of
+    // its patches), update, copy out, then the next step's copy in of the
+    // same chunk once its copy out has landed.  The chains of different
+    // chunks are independent, so copies in both directions and the updates
+    // of different chunks (and steps) overlap.  The device staging buffers
+    // are reused safely along each chain: a chunk's copy in waits for its
+    // previous copy out, which follows the update that read its input.
+    cudaError_t e = cudaEventRecord(start, org);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, start, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_dx, dx_host, arr, cudaMemcpyHostToDevice, cin);
+    for (int st = 0; st < steps && e == cudaSuccess; ++st) {
+        const int src = st & 1, dst = 1 - src;
+        const bool last = st == steps - 1;
+        for (int c = 0; c < C && e == cudaSuccess; ++c) {
+            const ChunkRange &r = ranges[c];
+            const size_t po = (size_t)r.p_lo * sizeof(double), pn = (size_t)(r.p_hi - r.p_lo) * sizeof(double);
+            cudaEvent_t ev_in = b->hs_events[2 * c], ev_done = b->hs_events[2 * c + 1];
+            cudaEvent_t ev_out = b->hs_events[2 * kMaxHostChunks + 2 + c];
+            if (st > 0) e = cudaStreamWaitEvent(cin, ev_out, 0);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(qi + r.byte_off, hq[src] + r.byte_off, r.bytes,
+                                                      cudaMemcpyHostToDevice, cin);
+            if (e == cudaSuccess && pn)
+                e = cudaMemcpyAsync(reinterpret_cast<unsigned char *>(d_dt) + po,
+                                    reinterpret_cast<const unsigned char *>(hdt[src]) + po, pn,
+                                    cudaMemcpyHostToDevice, cin);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_in, cin);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(org, ev_in, 0);
+            if (e == cudaSuccess && b->halo_mode == FV_HALO_FIXED)      // Q_in's halos go back with the state
+                e = cudaMemcpyAsync(qo + r.byte_off, qi + r.byte_off, r.bytes, cudaMemcpyDeviceToDevice, org);
+            if (e != cudaSuccess) break;
+            const fv::StepArgs args{qi, qo, d_dx, d_dt, last && lambda_host ? d_lam : nullptr, d_dtn, cfl};
+            rc = launch_chunk(b, org, split, r, args);
+            if (rc) break;
+            e = cudaEventRecord(ev_done, org);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, ev_done, 0);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hq[dst] + r.byte_off, qo + r.byte_off, r.bytes,
+                                                      cudaMemcpyDeviceToHost, cout);
+            if (e == cudaSuccess && pn)
+                e = cudaMemcpyAsync(reinterpret_cast<unsigned char *>(hdt[dst]) + po,
+                                    reinterpret_cast<const unsigned char *>(d_dtn) + po, pn,
+                                    cudaMemcpyDeviceToHost, cout);
+            if (e == cudaSuccess && last && lambda_host && pn)
+                e = cudaMemcpyAsync(reinterpret_cast<unsigned char *>(lambda_host) + po,
+                                    reinterpret_cast<const unsigned char *>(d_lam) + po, pn,
+                                    cudaMemcpyDeviceToHost, cout);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_out, cout);
+        }
+        if (rc) break;
+    }
+    if (e == cudaSuccess && rc == FV_OK) e = cudaEventRecord(joined, cout);
+    if (e == cudaSuccess && rc == FV_OK) e = cudaStreamWaitEvent(org, joined, 0);
+    // whatever was enqueued finishes before the call returns (the host
+    // buffers stay the caller's once it has)
+    const cudaError_t s1 = cudaStreamSynchronize(cin), s2 = cudaStreamSynchronize(cout),
+                      s3 = cudaStreamSynchronize(org);
+    if (rc) return rc;
+    if (e == cudaSuccess) e = s1 != cudaSuccess ? s1 : (s2 != cudaSuccess ? s2 : s3);
+    return e == cudaSuccess ? FV_OK : cuda_fail(e, "host time stepping");
 }
 
 // --------------------------------------------------------------- autotuner

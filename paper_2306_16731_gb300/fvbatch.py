@@ -55,7 +55,8 @@ EXPORTS = ["fv_batch_create", "fv_batch_set_form", "fv_batch_set_stream", "fv_ba
            "fv_batch_destroy", "fv_last_error", "fv_batch_state_elems",
            "fv_batch_scratch_bytes", "fv_batch_describe", "fv_batch_launches_per_update",
            "fv_batch_test_wait_expiry", "fv_batch_set_cascade_layout", "fv_batch_create_pde",
-           "fv_batch_set_host_patches", "fv_patch_batch_update_scattered", "fv_test_fail_device_alloc"]
+           "fv_batch_set_host_patches", "fv_patch_batch_update_scattered", "fv_test_fail_device_alloc",
+           "fv_patch_batch_run_host"]
 
 
 class FVError(RuntimeError):
@@ -102,6 +103,7 @@ def load() -> ctypes.CDLL:
             "fv_patch_batch_update_scattered": (i, [_vp, _vp, _vp, _vp, _vp, d, i]),
             "fv_batch_set_neighbours": (i, [_vp, ctypes.POINTER(ctypes.c_int32)]),
             "fv_patch_batch_update_host": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, d, i]),
+            "fv_patch_batch_run_host": (i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, i, d, i]),
             "fv_halo_exchange": (i, [_vp, _vp]),
             "fv_patch_batch_update": (i, [_vp, _vp, _vp, _dp, _dp, _dp, _dp, d]),
             "fv_max_eigenvalue": (i, [_vp, _vp, _dp]),
@@ -237,6 +239,15 @@ def fv_patch_batch_update(b, Q_in, Q_out, dx, dt, lambda_out=None, dt_next_out=N
                                                _addr(lambda_out), _addr(dt_next_out), float(cfl)))
 
 
+def fv_patch_batch_run_host(b, Q_a_host, Q_b_host, dx_host, dt_a_host, dt_b_host, lambda_host=None, steps=1,
+                            cfl=0.4, chunks=8):
+    """CFL-chained steps with the state in host memory (pinned torch CPU
+    tensors or addresses), ping-ponging between Q_a/Q_b and dt_a/dt_b."""
+    return _check(load().fv_patch_batch_run_host(b, _addr(Q_a_host), _addr(Q_b_host), _addr(dx_host),
+                                                 _addr(dt_a_host), _addr(dt_b_host), _addr(lambda_host),
+                                                 int(steps), float(cfl), int(chunks)))
+
+
 def fv_patch_batch_update_host(b, Q_in_host, Q_out_host, dx_host, dt_host, lambda_host=None,
                                dt_next_host=None, cfl=0.4, chunks=8):
     """Update with the state in host memory (pinned torch CPU tensors or
@@ -368,6 +379,11 @@ class FVBatch:
                     cfl=0.4, chunks=8):
         fv_patch_batch_update_host(self.handle, Q_in_host, Q_out_host, dx_host, dt_host, lambda_host,
                                    dt_next_host, cfl, chunks)
+
+    def run_host(self, Q_a_host, Q_b_host, dx_host, dt_a_host, dt_b_host, lambda_host=None, steps=1, cfl=0.4,
+                 chunks=8):
+        fv_patch_batch_run_host(self.handle, Q_a_host, Q_b_host, dx_host, dt_a_host, dt_b_host, lambda_host, steps,
+                                cfl, chunks)
 
     def max_eigenvalue(self, Q, lambda_out):
         fv_max_eigenvalue(self.handle, Q, lambda_out)

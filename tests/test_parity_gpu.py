@@ -673,6 +673,137 @@ def test_host_state_update_matches_device_update(dim, sizes, precision, halo):
     b.close()
 
 
+def _host_chain_setup(dim, sizes, precision, halo, seed):
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w = inputs.uniform_batch(dim, sizes, seed=seed, dx=np.linspace(0.02, 0.03, len(sizes)), halo_mode=halo)
+    T = w.num_patches
+    b = fb.FVBatch(dim, w.patch_size, precision=precision, halo_mode=halo)
+    q0 = torch.from_numpy(w.Q0).to(torch_dtype(precision))
+    lam0 = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dt0 = torch.zeros_like(lam0)
+    dx = torch.tensor(w.dx, device="cuda")
+    b.max_eigenvalue(q0.cuda(), lam0)
+    b.cfl_time_step(lam0, dx, w.cfl, dt0)
+    torch.cuda.synchronize()
+    return w, b, q0, dt0.cpu()
+
+
+@pytest.mark.parametrize("dim,sizes,precision,halo", [(2, [16] * 300, 1, inputs.FIXED),
+                                                      (3, [8] * 40, 1, inputs.PERIODIC),
+                                                      (3, [16] * 12, 1, inputs.FIXED),
+                                                      (2, [8, 16, 4] * 5, 0, inputs.FIXED)])
+def test_host_time_stepping_equals_per_step_calls_and_the_oracle(dim, sizes, precision, halo):
+    """fv_patch_batch_run_host: S CFL-chained steps with the state in host
+    memory, every step copied in and out, the chunks' chains overlapping
+    across steps.  Bitwise the same final state, time steps and eigenvalues
+    as S calls of fv_patch_batch_update_host with the buffers alternated,
+    for 1, 3 and 8 chunks, and within the precision's tolerance of the
+    oracle's S CFL-chained steps; fixed halos come back unchanged."""
+    import torch
+    S = 5
+    w, b, q0, dt0 = _host_chain_setup(dim, sizes, precision, halo, 150 + dim)
+    T = w.num_patches
+    pin = lambda t: t.clone().pin_memory()
+    hdx = pin(torch.from_numpy(w.dx.copy()))
+    # reference: S single-step calls
+    rq = [pin(q0), pin(q0)]
+    rdt = [pin(dt0), pin(torch.zeros(T, dtype=torch.float64))]
+    rlam = pin(torch.zeros(T, dtype=torch.float64))
+    for s_ in range(S):
+        i = s_ & 1
+        b.update_host(rq[i], rq[1 - i], hdx, rdt[i], rlam, rdt[1 - i], w.cfl, 4)
+    ref_q, ref_dt = rq[S & 1], rdt[S & 1]
+    for chunks in (1, 3, 8):
+        hq = [pin(q0), pin(q0)]
+        hdt = [pin(dt0), pin(torch.zeros(T, dtype=torch.float64))]
+        hlam = pin(torch.zeros(T, dtype=torch.float64))
+        b.run_host(hq[0], hq[1], hdx, hdt[0], hdt[1], hlam, S, w.cfl, chunks)
+        got = patches_interior(hq[S & 1].to(torch.float64).numpy(), dim, w.patch_size)
+        ref = patches_interior(ref_q.to(torch.float64).numpy(), dim, w.patch_size)
+        assert all(np.array_equal(g, r) for g, r in zip(got, ref)), chunks
+        assert np.array_equal(hdt[S & 1].numpy(), ref_dt.numpy()), chunks
+        assert np.array_equal(hlam.numpy(), rlam.numpy()), chunks
+        if halo == inputs.FIXED:
+            assert np.array_equal(hq[S & 1].numpy(), ref_q.numpy())        # halos included
+            assert_halos_equal(hq[S & 1].to(torch.float64).numpy(), initial_fp64(w.Q0, precision), dim,
+                               w.patch_size)
+    b.status()
+    b.close()
+    oref, olam, _ = oracle.batch_run(dim, w.patch_size, w.dx, initial_fp64(w.Q0, precision), S, gamma=w.gamma,
+                                     halo_mode=halo, cfl=w.cfl)
+    assert batch_rel_linf(ref_q.to(torch.float64).numpy(), oref, dim, w.patch_size) <= TOL[precision]
+    assert np.max(np.abs(rlam.numpy() - olam) / olam) <= TOL[precision]
+
+
+def assert_halos_equal(a, b, dim, sizes):
+    """Every halo volume of the batch state a equals b's."""
+    off = 0
+    for p in sizes:
+        n = (int(p) + 2) ** dim * (dim + 2)
+        pa = a[off:off + n].reshape((int(p) + 2,) * dim + (dim + 2,))
+        pb = b[off:off + n].reshape((int(p) + 2,) * dim + (dim + 2,))
+        mask = np.ones((int(p) + 2,) * dim, bool)
+        mask[(slice(1, -1),) * dim] = False
+        assert np.array_equal(pa[mask], pb[mask])
+        off += n
+
+
+def test_host_time_stepping_rejects_bad_arguments_and_handles_no_steps():
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    w, b, q0, dt0 = _host_chain_setup(2, [16] * 8, 1, inputs.FIXED, 160)
+    pin = lambda t: t.clone().pin_memory()
+    hq = [pin(q0), pin(q0)]
+    hdx = pin(torch.from_numpy(w.dx.copy()))
+    hdt = [pin(dt0), pin(dt0)]
+    before = hq[0].clone()
+    b.run_host(hq[0], hq[1], hdx, hdt[0], hdt[1], None, 0, 0.4, 4)            # no steps: nothing moves
+    assert torch.equal(hq[0], before)
+    for kw in ({"steps": -1}, {"chunks": 0}, {"chunks": 65}, {"cfl": 0.0}):
+        args = dict(steps=2, cfl=0.4, chunks=4)
+        args.update(kw)
+        with pytest.raises(fb.FVError) as e:
+            b.run_host(hq[0], hq[1], hdx, hdt[0], hdt[1], None, args["steps"], args["cfl"], args["chunks"])
+        assert e.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as e:
+        b.run_host(hq[0], hq[0], hdx, hdt[0], hdt[1], None, 2, 0.4, 4)          # Q_a is Q_b
+    assert e.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as e:
+        b.run_host(hq[0], hq[1], hdx, hdt[0], hdt[0], None, 2, 0.4, 4)          # dt_a is dt_b
+    assert e.value.code == fb.FV_EINVAL
+    with pytest.raises(fb.FVError) as e:
+        b.run_host(hq[0], None, hdx, hdt[0], hdt[1], None, 2, 0.4, 4)
+    assert e.value.code == fb.FV_EINVAL
+    b.close()
+
+
+@pytest.mark.parametrize("chunks", [1, 4])
+def test_chained_host_updates_keep_fixed_halos_and_match_the_oracle(chunks):
+    """Single-step host updates chained by the caller (output of one the
+    input of the next): with fixed halos the staged output carries the
+    input's halo volumes back, so the chain is the oracle's."""
+    import torch
+    S = 4
+    w, b, q0, dt0 = _host_chain_setup(2, [16] * 64, 1, inputs.FIXED, 170)
+    T = w.num_patches
+    pin = lambda t: t.clone().pin_memory()
+    hdx = pin(torch.from_numpy(w.dx.copy()))
+    hq = [pin(q0), pin(torch.full_like(q0, float("nan")))]                  # output halos start as NaN
+    hdt = [pin(dt0), pin(torch.zeros(T, dtype=torch.float64))]
+    hlam = pin(torch.zeros(T, dtype=torch.float64))
+    for s_ in range(S):
+        i = s_ & 1
+        b.update_host(hq[i], hq[1 - i], hdx, hdt[i], hlam, hdt[1 - i], w.cfl, chunks)
+    b.status()
+    assert_halos_equal(hq[S & 1].to(torch.float64).numpy(), initial_fp64(w.Q0, 1), 2, w.patch_size)
+    oref, olam, _ = oracle.batch_run(2, w.patch_size, w.dx, initial_fp64(w.Q0, 1), S, gamma=w.gamma,
+                                     halo_mode=inputs.FIXED, cfl=w.cfl)
+    assert batch_rel_linf(hq[S & 1].to(torch.float64).numpy(), oref, 2, w.patch_size) <= TOL[1]
+    assert np.max(np.abs(hlam.numpy() - olam) / olam) <= TOL[1]
+    b.close()
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("T", [1, 5, 37, 700])
 def test_periodic_8cubed_warp_kernel_shapes_and_oracle(precision, T):

@@ -459,13 +459,16 @@ def run_ours(args):
                             w.cfl, chunks_)
 
     # the same steps as one fv_patch_batch_update_host call each (a step's
-    # copies in wait for the previous call's copies out)
-    host_steps(4, chunks)                  # captures the two ping-pong graphs
+    # copies in wait for the previous call's copies out), at that call's
+    # best chunk count
+    call_chunks = 4
+    host_steps(4, call_chunks)             # captures the two ping-pong graphs
     barrier()
     t_c = time.perf_counter()
-    host_steps(ke, chunks)
+    host_steps(ke, call_chunks)
     barrier()
     e2e["per_step_calls_value"] = whole_job_rate(vols * ke, time.perf_counter() - t_c, dist, dev)
+    e2e["per_step_calls_chunks"] = call_chunks
     b32.status()
     # the same call with chunks = 0: the kernels read and write the mapped
     # host buffers directly over the coherent CPU-GPU link, no staging

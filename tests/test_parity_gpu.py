@@ -1347,6 +1347,34 @@ def test_shallow_water_host_state_update_matches_device_update(chunks):
     b.close()
 
 
+def test_shallow_water_host_time_stepping_equals_per_step_calls():
+    """fv_patch_batch_run_host drives the generic-PDE kernel (uniform batch:
+    chunk chains over the fused shallow-water sweep) exactly like per-step
+    host updates with the buffers alternated, fixed halos carried along."""
+    import torch
+    S = 3
+    w = inputs.shallow_water_batch([16] * 40, seed=193, dx=0.05)
+    T = w.num_patches
+    b = _swe_batch(w, 1)
+    pin = lambda t: t.clone().pin_memory()
+    q0 = torch.from_numpy(w.Q0.astype(np.float32))
+    dx = pin(torch.tensor(w.dx))
+    dt0 = torch.full((T,), 2e-3, dtype=torch.float64)
+    rq, rdt = [pin(q0), pin(q0)], [pin(dt0), pin(torch.zeros(T, dtype=torch.float64))]
+    rl = pin(torch.zeros(T, dtype=torch.float64))
+    for s_ in range(S):
+        i = s_ & 1
+        b.update_host(rq[i], rq[1 - i], dx, rdt[i], rl, rdt[1 - i], 0.4, 4)
+    for chunks in (1, 4):
+        hq, hdt = [pin(q0), pin(q0)], [pin(dt0), pin(torch.zeros(T, dtype=torch.float64))]
+        hl = pin(torch.zeros(T, dtype=torch.float64))
+        b.run_host(hq[0], hq[1], dx, hdt[0], hdt[1], hl, S, 0.4, chunks)
+        assert torch.equal(hq[S & 1], rq[S & 1]) and torch.equal(hdt[S & 1], rdt[S & 1])
+        assert torch.equal(hl, rl)
+    b.status()
+    b.close()
+
+
 def test_out_of_memory_paths_fail_cleanly_and_batches_stay_usable():
     """Device allocation failures (made on the host with the test hook) give
     FV_ENOMEM at every call that allocates; nothing half-made stays behind,

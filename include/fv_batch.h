@@ -304,8 +304,12 @@ int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, void *Q_out
  * in, its update, its state and next time steps out, then its next step's
  * copy in -- while the chains of the other ranges proceed independently, so
  * one step's copies out overlap the next step's copies in; any other batch
- * runs as one range.  Results are bitwise those of `steps` calls of
- * fv_patch_batch_update_host with the buffers alternated.  steps = 0 or an
+ * runs as one range.  With a neighbour table (fv_batch_set_neighbours) each
+ * step first fills the face halos from the neighbours where the kernel does
+ * not read them itself, as fv_batch_run does.  Results are bitwise those of
+ * fv_batch_run on device copies of the buffers (and, without a neighbour
+ * table, of `steps` calls of fv_patch_batch_update_host with the buffers
+ * alternated).  steps = 0 or an
  * empty batch: no-op.  FV_EINVAL for NULL pointers, steps < 0, chunks
  * outside 1..64, a non-positive cfl, or overlapping Q_a/Q_b or dt_a/dt_b;
  * the device staging is that of fv_patch_batch_update_host (FV_ENOMEM).

@@ -1152,6 +1152,10 @@ extern "C" int fv_patch_batch_run_host(fv_batch_t *b, void *Q_a_host, void *Q_b_
             if (e == cudaSuccess) e = cudaStreamWaitEvent(org, ev_in, 0);
             if (e == cudaSuccess && b->halo_mode == FV_HALO_FIXED)      // Q_in's halos go back with the state
                 e = cudaMemcpyAsync(qo + r.byte_off, qi + r.byte_off, r.bytes, cudaMemcpyDeviceToDevice, org);
+            // a neighbour table: halos filled from the neighbours before each
+            // update, as fv_batch_run does (the batch then runs as one chunk)
+            if (e == cudaSuccess && b->view.nbr && !(b->form == FV_FORM_FUSED && fv::fused_reads_neighbours(b->plan)))
+                e = fv::launch_halo_exchange(b->view, b->precision, b->view.nbr, qi, org);
             if (e != cudaSuccess) break;
             const fv::StepArgs args{qi, qo, d_dx, d_dt, last && lambda_host ? d_lam : nullptr, d_dtn, cfl};
             rc = launch_chunk(b, org, split, r, args);

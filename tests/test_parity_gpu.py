@@ -749,6 +749,46 @@ def assert_halos_equal(a, b, dim, sizes):
         off += n
 
 
+@pytest.mark.parametrize("dim,G,p,form", [(3, 2, 8, "fused"), (2, 4, 16, "fused"), (2, 3, 8, "tile")])
+def test_host_time_stepping_on_a_neighbour_grid_equals_fv_batch_run(dim, G, p, form):
+    """With a neighbour table, fv_patch_batch_run_host fills the face halos
+    from the neighbours before each step (where the kernel does not read
+    them itself), as fv_batch_run does on device buffers: the same interiors,
+    eigenvalues and time steps bitwise, and the oracle's grid run."""
+    import torch
+    from paper_2306_16731_gb300 import fvbatch as fb
+    T = G ** dim
+    S = 5
+    w = inputs.uniform_batch(dim, [p] * T, seed=180 + dim + p, dx=np.linspace(0.01, 0.02, T))
+    nb = _grid_neighbours(G, dim, open_faces=[(0, 1), (T - 1, 2)])
+    b = fb.FVBatch(dim, w.patch_size, precision=1, form=FORMS[form])
+    b.set_neighbours(nb.tolist())
+    q0 = torch.from_numpy(w.Q0).to(torch.float32)
+    dx = torch.tensor(w.dx, device="cuda")
+    lam = torch.zeros(T, dtype=torch.float64, device="cuda")
+    dta, dtb = torch.zeros_like(lam), torch.zeros_like(lam)
+    b.max_eigenvalue(q0.cuda(), lam)
+    b.cfl_time_step(lam, dx, w.cfl, dta)
+    dt0 = dta.cpu()
+    qa, qb = q0.cuda(), q0.cuda()
+    b.run(qa, qb, dx, dta, dtb, lam, S, w.cfl, use_graph=False)
+    ref_q = (qb if S % 2 else qa).cpu()
+    ref_dt, ref_lam = (dtb if S % 2 else dta).cpu(), lam.cpu()
+    pin = lambda t: t.clone().pin_memory()
+    hq = [pin(q0), pin(q0)]
+    hdt = [pin(dt0), pin(torch.zeros(T, dtype=torch.float64))]
+    hl = pin(torch.zeros(T, dtype=torch.float64))
+    b.run_host(hq[0], hq[1], pin(dx.cpu()), hdt[0], hdt[1], hl, S, w.cfl, 4)
+    b.status()
+    got = patches_interior(hq[S & 1].to(torch.float64).numpy(), dim, w.patch_size)
+    ref = patches_interior(ref_q.to(torch.float64).numpy(), dim, w.patch_size)
+    assert all(np.array_equal(g, r) for g, r in zip(got, ref))
+    assert torch.equal(hdt[S & 1], ref_dt) and torch.equal(hl, ref_lam)
+    oref, olam = _oracle_grid_run(w, nb, S, 1)
+    assert batch_rel_linf(hq[S & 1].to(torch.float64).numpy(), oref, dim, w.patch_size) <= TOL[1]
+    b.close()
+
+
 def test_host_time_stepping_rejects_bad_arguments_and_handles_no_steps():
     import torch
     from paper_2306_16731_gb300 import fvbatch as fb

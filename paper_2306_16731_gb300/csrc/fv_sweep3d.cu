@@ -470,8 +470,12 @@ __device__ __forceinline__ void ring_face<float>(const float (&qr)[5], const flo
 }
 
 // PC > 0: the edge length compiled in (all index arithmetic folds); 0: sp.p.
+// Register budget: the 16-edge instance (128 threads) is held to five
+// resident blocks per SM (96 registers, no spills: 20 warps; 121 registers
+// and 16 warps otherwise); other edges take up to 512 threads.
 template <typename S, typename C, int PC, bool BULK>
-__global__ void __launch_bounds__(512, 1) k_sweep3d_b8(Sweep3Params sp, int plane_bytes, int chunk)
+__global__ void __launch_bounds__(PC == 16 ? 128 : 512, PC == 16 ? 5 : 1)
+    k_sweep3d_b8(Sweep3Params sp, int plane_bytes, int chunk)
 {
     constexpr int N = 5;
     extern __shared__ __align__(16) unsigned char smemb[];

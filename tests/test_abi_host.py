@@ -86,6 +86,8 @@ def test_null_batch_is_rejected_or_ignored(lib):
     assert lib.fv_max_eigenvalue(None, None, None) == -1
     assert lib.fv_batch_status(None) == -1
     assert lib.fv_batch_state_elems(None) == 0
+    assert lib.fv_patch_batch_update_host(None, None, None, None, None, None, None, 0.4, 4) == -1
+    assert lib.fv_patch_batch_run_host(None, None, None, None, None, None, None, 5, 0.4, 4) == -1
 
 
 def _declared_arities():

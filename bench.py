@@ -429,7 +429,7 @@ def run_ours(args):
     host_dts = [dt0.cpu().pin_memory(), torch.empty(T, dtype=torch.float64).pin_memory()]
     host_dt = host_dts[0]
     ke = max(20, min(50, args.steps)) // 2 * 2           # even: the state ends where it started
-    chunks = 2                             # two chunk chains: 0.567 ms per step (4: 0.576, 8: 0.62-0.65)
+    chunks = 2                             # two chunk chains: 0.557 ms per step (4: 0.576, 8: 0.61-0.63)
 
     b32.run_host(host_q[0], host_q[1], host_dx, host_dts[0], host_dts[1], host_lam, 2, w.cfl, chunks)   # staging
     b32.status()

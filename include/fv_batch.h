@@ -314,8 +314,9 @@ int fv_patch_batch_update_host(fv_batch_t *b, const void *Q_in_host, void *Q_out
  * outside 1..64, a non-positive cfl, or overlapping Q_a/Q_b or dt_a/dt_b;
  * the device staging is that of fv_patch_batch_update_host (FV_ENOMEM).
  * Synchronous: returns when the final state and outputs are on the host.
- * With fixed halos every state written keeps the first state's halo
- * volumes; with periodic halos the halo volumes written are unspecified.
+ * With fixed halos and no neighbour table every state written keeps the
+ * first state's halo volumes; otherwise the halo volumes written are
+ * unspecified (the updates never read them: they are exchanged or wrapped).
  */
 int fv_patch_batch_run_host(fv_batch_t *b, void *Q_a_host, void *Q_b_host, const double *dx_host,
                             double *dt_a_host, double *dt_b_host, double *lambda_host, int steps,

@@ -1150,7 +1150,10 @@ extern "C" int fv_patch_batch_run_host(fv_batch_t *b, void *Q_a_host, void *Q_b_
                                     cudaMemcpyHostToDevice, cin);
             if (e == cudaSuccess) e = cudaEventRecord(ev_in, cin);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(org, ev_in, 0);
-            if (e == cudaSuccess && b->halo_mode == FV_HALO_FIXED)      // Q_in's halos go back with the state
+            // fixed halos: the staged output starts as the first input, so the
+            // halo volumes no update writes go back as Q_a's; later updates
+            // rewrite only interiors and copied x-halo volumes, so once is enough
+            if (e == cudaSuccess && st == 0 && b->halo_mode == FV_HALO_FIXED)
                 e = cudaMemcpyAsync(qo + r.byte_off, qi + r.byte_off, r.bytes, cudaMemcpyDeviceToDevice, org);
             // a neighbour table: halos filled from the neighbours before each
             // update, as fv_batch_run does (the batch then runs as one chunk)

@@ -673,12 +673,12 @@ def test_host_state_update_matches_device_update(dim, sizes, precision, halo):
     b.close()
 
 
-def _host_chain_setup(dim, sizes, precision, halo, seed):
+def _host_chain_setup(dim, sizes, precision, halo, seed, form="fused"):
     import torch
     from paper_2306_16731_gb300 import fvbatch as fb
     w = inputs.uniform_batch(dim, sizes, seed=seed, dx=np.linspace(0.02, 0.03, len(sizes)), halo_mode=halo)
     T = w.num_patches
-    b = fb.FVBatch(dim, w.patch_size, precision=precision, halo_mode=halo)
+    b = fb.FVBatch(dim, w.patch_size, precision=precision, halo_mode=halo, form=FORMS[form])
     q0 = torch.from_numpy(w.Q0).to(torch_dtype(precision))
     lam0 = torch.zeros(T, dtype=torch.float64, device="cuda")
     dt0 = torch.zeros_like(lam0)
@@ -689,11 +689,15 @@ def _host_chain_setup(dim, sizes, precision, halo, seed):
     return w, b, q0, dt0.cpu()
 
 
-@pytest.mark.parametrize("dim,sizes,precision,halo", [(2, [16] * 300, 1, inputs.FIXED),
-                                                      (3, [8] * 40, 1, inputs.PERIODIC),
-                                                      (3, [16] * 12, 1, inputs.FIXED),
-                                                      (2, [8, 16, 4] * 5, 0, inputs.FIXED)])
-def test_host_time_stepping_equals_per_step_calls_and_the_oracle(dim, sizes, precision, halo):
+@pytest.mark.parametrize("dim,sizes,precision,halo,form", [(2, [16] * 300, 1, inputs.FIXED, "fused"),
+                                                           (3, [8] * 40, 1, inputs.PERIODIC, "fused"),
+                                                           (3, [16] * 12, 1, inputs.FIXED, "fused"),
+                                                           (2, [8, 16, 4] * 5, 0, inputs.FIXED, "fused"),
+                                                           (2, [16] * 64, 2, inputs.FIXED, "fused"),
+                                                           (3, [8] * 16, 2, inputs.PERIODIC, "fused"),
+                                                           (2, [8] * 40, 0, inputs.FIXED, "cascade"),
+                                                           (3, [4] * 20, 1, inputs.FIXED, "tile")])
+def test_host_time_stepping_equals_per_step_calls_and_the_oracle(dim, sizes, precision, halo, form):
     """fv_patch_batch_run_host: S CFL-chained steps with the state in host
     memory, every step copied in and out, the chunks' chains overlapping
     across steps.  Bitwise the same final state, time steps and eigenvalues
@@ -702,7 +706,7 @@ def test_host_time_stepping_equals_per_step_calls_and_the_oracle(dim, sizes, pre
     oracle's S CFL-chained steps; fixed halos come back unchanged."""
     import torch
     S = 5
-    w, b, q0, dt0 = _host_chain_setup(dim, sizes, precision, halo, 150 + dim)
+    w, b, q0, dt0 = _host_chain_setup(dim, sizes, precision, halo, 150 + dim, form)
     T = w.num_patches
     pin = lambda t: t.clone().pin_memory()
     hdx = pin(torch.from_numpy(w.dx.copy()))
@@ -725,15 +729,17 @@ def test_host_time_stepping_equals_per_step_calls_and_the_oracle(dim, sizes, pre
         assert np.array_equal(hdt[S & 1].numpy(), ref_dt.numpy()), chunks
         assert np.array_equal(hlam.numpy(), rlam.numpy()), chunks
         if halo == inputs.FIXED:
-            assert np.array_equal(hq[S & 1].numpy(), ref_q.numpy())        # halos included
+            assert torch.equal(hq[S & 1], ref_q)                          # halos included
             assert_halos_equal(hq[S & 1].to(torch.float64).numpy(), initial_fp64(w.Q0, precision), dim,
                                w.patch_size)
     b.status()
     b.close()
     oref, olam, _ = oracle.batch_run(dim, w.patch_size, w.dx, initial_fp64(w.Q0, precision), S, gamma=w.gamma,
                                      halo_mode=halo, cfl=w.cfl)
-    assert batch_rel_linf(ref_q.to(torch.float64).numpy(), oref, dim, w.patch_size) <= TOL[precision]
-    assert np.max(np.abs(rlam.numpy() - olam) / olam) <= TOL[precision]
+    # BF16 storage rounds the state every step: within S * 2^-8 of the state
+    tol = TOL[precision] if precision != 2 else S * 2.0 ** -8
+    assert batch_rel_linf(ref_q.to(torch.float64).numpy(), oref, dim, w.patch_size) <= tol
+    assert np.max(np.abs(rlam.numpy() - olam) / olam) <= tol
 
 
 def assert_halos_equal(a, b, dim, sizes):

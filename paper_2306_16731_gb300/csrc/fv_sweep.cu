@@ -596,17 +596,19 @@ __device__ __forceinline__ void sweep2d_tpl(const SweepParams sp, const WorkItem
 // Items [item_begin, item_begin + num_items) of the sorted work list belong
 // to the launch.
 
-// The launch over every size class inlines four sweeps and would take 104
-// registers in FP32; it is held to 64 (two full blocks per SM, 32 warps),
-// which measured 11% faster on a 50,000-patch uneven batch.
+// Register cap: the launch over every size class inlines four sweeps and
+// would take 104 registers in FP32; held to 72 (28 warps per SM, a few bytes
+// spilled) it measured 11% faster than unheld on a 50,000-patch uneven
+// batch, and 1.8% faster than held to 64.  The other instances take what
+// 512-thread blocks allow.
 template <typename S, int P>
-constexpr int sweep2d_min_blocks()
+constexpr int sweep2d_max_regs()
 {
-    return (P < 0 && sizeof(S) < 8) ? 2 : FV_SWEEP_MINB;
+    return (P < 0 && sizeof(S) < 8) ? 72 : 65536 / FV_SWEEP_MAXT;
 }
 
 template <typename S, int P, int R = RingDepth<S>::value>
-__global__ void __launch_bounds__(FV_SWEEP_MAXT, (sweep2d_min_blocks<S, P>())) k_sweep2d(SweepParams sp)
+__global__ void __maxnreg__((sweep2d_max_regs<S, P>())) k_sweep2d(SweepParams sp)
 {
     using C = typename StorageTraits<S>::Compute;
     extern __shared__ __align__(16) unsigned char smem_raw[];
